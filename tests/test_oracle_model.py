@@ -1,0 +1,250 @@
+"""Pins for the oracle's MADE model, sampler, generator and gradient.
+
+Each test checks the FP64 oracle against something other than itself: a
+published known-answer vector, a closed form, an invariant of the
+autoregressive construction, exhaustive enumeration, or central finite
+differences.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_13308_gb300 import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _params(n, h, seed, scale=1.0):
+    th = inputs.made_params(n, h, seed, w_std=scale * 1.5 / math.sqrt(n), v_std=scale * 3.0 / math.sqrt(h),
+                            bias_std=0.5)
+    return oracle.theta_to_made(th, n, h)
+
+
+def _small_instance(n, seed, p=0.5, weights="int"):
+    e = inputs.erdos_renyi(n, p, seed)
+    if weights == "int":
+        w = inputs.int_weights(len(e), -3, 5, seed + 1)
+    else:
+        w = np.random.default_rng(seed).standard_normal(len(e)).astype(np.float32)
+    inst = inputs.to_csr(n, e, w)
+    return inst
+
+
+# ------------------------------------------------------------ generator
+
+def test_philox_known_answers():
+    """Philox4x32-10 matches the generator's published known-answer vectors."""
+    kat = json.load(open(os.path.join(GOLD, "philox4x32_10_kat.json")))
+    for v in kat["vectors"]:
+        ctr = [int(x, 16) for x in v["ctr"]]
+        key = [int(x, 16) for x in v["key"]]
+        out = [int(x, 16) for x in v["out"]]
+        assert list(oracle.philox4x32_10(ctr, key)) == out
+
+
+def test_uniform_grid_and_moments():
+    u = oracle.uniforms(64, 257, seed=12345, it=7)
+    assert u.dtype == np.float32 and u.min() >= 0.0 and u.max() < 1.0
+    assert np.all((u.astype(np.float64) * (1 << 24)) % 1.0 == 0.0)
+    assert abs(u.mean() - 0.5) < 0.01 and abs(u.var() - 1 / 12) < 0.005
+    # distinct iterations and seeds give distinct streams
+    assert not np.array_equal(u, oracle.uniforms(64, 257, seed=12345, it=8))
+    assert not np.array_equal(u, oracle.uniforms(64, 257, seed=12346, it=7))
+    # word (i mod 4) of counter (i/4, b, it): spot-check one entry against the raw generator
+    w = oracle.philox4x32_10([5, 3, 7, 0], [12345, 0])
+    assert u[3, 22] == np.float32((int(w[2]) >> 8) / float(1 << 24))
+
+
+# ----------------------------------------------------------------- model
+
+def test_degrees_sorted_and_in_range():
+    for n, h in [(20, 40), (1000, 1000), (10000, 2000), (7, 3), (2, 5)]:
+        m = oracle.degrees(n, h)
+        assert m[0] == 1 and np.all(np.diff(m) >= 0) and m.max() <= max(n - 1, 1)
+
+
+@pytest.mark.parametrize("act", [oracle.RELU, oracle.SIGMOID])
+def test_autoregressive_property(act):
+    """z_i depends only on s_<i: changing s_i..s_n leaves z_i unchanged."""
+    n, h = 13, 29
+    P = _params(n, h, 3)
+    rng = np.random.default_rng(0)
+    s = inputs.spins(1, n, 4)[0]
+    _, z = oracle.forward(P, s, act)
+    assert z[0] == P[3][0]  # p(s_1) = sigma(c_1)
+    for i in range(n):
+        for _ in range(4):
+            t = s.copy()
+            t[i:] = np.where(rng.random(n - i) < 0.5, 1, -1)
+            _, z2 = oracle.forward(P, t, act)
+            assert np.array_equal(z2[: i + 1], z[: i + 1])
+    # with h >= n - 1 every degree 1..n-1 is used, so z_i depends on s_{i-1}
+    # for every i >= 2 (M1 uses m(k) >= j, M2 uses i > m(k): maximal
+    # connectivity).  Checked with the sigmoid, which has no dead units.
+    if act != oracle.SIGMOID:
+        return
+    for i in range(1, n):
+        t = s.copy()
+        t[i - 1] = -t[i - 1]
+        _, z3 = oracle.forward(P, t, act)
+        assert z3[i] != z[i], i
+
+
+@pytest.mark.parametrize("n,h,act", [(12, 20, oracle.RELU), (12, 20, oracle.SIGMOID), (20, 40, oracle.SIGMOID)])
+def test_normalisation_by_enumeration(n, h, act):
+    """sum_s pi(s) = 1 (autoregressive normalisation, Sec. 2.3)."""
+    P = _params(n, h, 5)
+    inst = _small_instance(n, 6)
+    out = oracle.enumerate_exact(P, inst, act)
+    assert abs(out[0] - 1.0) < 1e-12
+
+
+def test_independent_spins_closed_forms():
+    """W2 = 0 makes the spins independent with pi_i(+1) = sigma(c_i):
+    log pi(s) = sum log sigma(s_i c_i), = -n ln 2 at c = 0, and
+    <E> = sum_{i<j} J_ij mu_i mu_j + sum h_i mu_i with mu = tanh(c/2)."""
+    n, h = 10, 15
+    W1, b1, W2, b2 = _params(n, h, 7)
+    W2 = np.zeros_like(W2)
+    S = inputs.spins(50, n, 8)
+    lp = oracle.logprob((W1, b1, W2, b2), S)
+    ref = np.array([sum(math.log(1 / (1 + math.exp(-s[i] * b2[i]))) for i in range(n)) for s in S])
+    assert np.allclose(lp, ref, rtol=0, atol=1e-12)
+    lp0 = oracle.logprob((W1, b1, W2, np.zeros(n)), S)
+    assert np.allclose(lp0, -n * math.log(2.0), rtol=0, atol=1e-12)
+
+    e = inputs.erdos_renyi(n, 0.6, 9)
+    w = inputs.int_weights(len(e), -4, 4, 10)
+    field = inputs.int_weights(n, -2, 2, 11)
+    inst = inputs.to_csr(n, e, w, field=field)
+    mu = np.tanh(b2 / 2)
+    J = inputs.dense_from_sparse(inst)
+    L_ref = 0.5 * mu @ J @ mu + field @ mu
+    out, g = oracle.enumerate_exact((W1, b1, W2, b2), inst, grad=True)
+    assert abs(out[1] - L_ref) < 1e-11
+    # d<E>/dc_k = 1/2 (1 - mu_k^2) (sum_j J_kj mu_j + h_k)
+    dc_ref = 0.5 * (1 - mu ** 2) * (J @ mu + field)
+    assert np.allclose(g[3], dc_ref, rtol=0, atol=1e-11)
+    # no dependence on W1, b1 when W2 = 0
+    assert np.all(g[0] == 0) and np.all(g[1] == 0)
+
+
+@pytest.mark.parametrize("act", [oracle.SIGMOID, oracle.RELU])
+def test_exact_gradient_two_routes(act):
+    """The enumerated score-function gradient sum_s p (E - L) grad log p equals
+    central differences of the enumerated L(theta) (Sec. 2.1)."""
+    n, h = 8, 11
+    P = _params(n, h, 12)
+    inst = _small_instance(n, 13)
+    _, g = oracle.enumerate_exact(P, inst, act, grad=True)
+    theta = oracle.made_to_theta(*P)
+    gflat = oracle.made_to_theta(*g)
+    m = oracle.degrees(n, h)
+    rng = np.random.default_rng(14)
+    # masked W1/W2 entries have zero gradient
+    W1mask = np.array([[m[k] >= j for j in range(1, n + 1)] for k in range(h)])
+    W2mask = np.array([[i > m[k] for k in range(h)] for i in range(1, n + 1)])
+    assert np.all(g[0][~W1mask] == 0) and np.all(g[2][~W2mask] == 0)
+    idx = list(rng.choice(theta.size, 40, replace=False)) + list(range(2 * n * h, 2 * n * h + h + n, 3))
+    eps = 1e-5
+    for q in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[q] += eps
+        tm[q] -= eps
+        Lp = oracle.enumerate_exact(oracle.theta_to_made(tp, n, h), inst, act)[1]
+        Lm = oracle.enumerate_exact(oracle.theta_to_made(tm, n, h), inst, act)[1]
+        fd = (Lp - Lm) / (2 * eps)
+        # theta index q maps to flat position; made_to_theta(g) uses the same layout
+        assert abs(fd - gflat[q]) <= 1e-7 + 1e-6 * abs(fd), (q, fd, gflat[q])
+
+
+def test_batch_gradient_finite_differences():
+    """sum_b c_b grad log pi(s_b) against central differences (eps = 1e-3,
+    FP64) of sum_b c_b log pi(s_b) on 32 random parameters of a 3-regular
+    instance; parameters whose +-eps move flips a ReLU are excluded."""
+    n, h, B = 60, 60, 64
+    P = _params(n, h, 15)
+    S = inputs.spins(B, n, 16)
+    coef = np.random.default_rng(17).standard_normal(B) / B
+    g = oracle.made_to_theta(*oracle.logprob_grad(P, S, coef))
+    theta = oracle.made_to_theta(*P)
+    m = oracle.degrees(n, h)
+    rng = np.random.default_rng(18)
+    live = [q for q in range(theta.size)]
+    idx = rng.choice(live, 32, replace=False)
+
+    def act_signs(th):
+        Q = oracle.theta_to_made(th, n, h)
+        return np.array([oracle.forward(Q, s)[0] > 0 for s in S])
+
+    base = act_signs(theta)
+    eps = 1e-3
+    checked = 0
+    for q in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[q] += eps
+        tm[q] -= eps
+        if not (np.array_equal(act_signs(tp), base) and np.array_equal(act_signs(tm), base)):
+            continue
+        fp = coef @ oracle.logprob(oracle.theta_to_made(tp, n, h), S)
+        fm = coef @ oracle.logprob(oracle.theta_to_made(tm, n, h), S)
+        fd = (fp - fm) / (2 * eps)
+        assert abs(fd - g[q]) <= 1e-8 + 1e-5 * abs(g[q]), (q, fd, g[q])
+        checked += 1
+    assert checked >= 24
+    # entries outside the masks get exactly zero
+    W1g = g[: n * h].reshape(n, h)  # W1^T layout: [j][k]
+    for j in range(n):
+        assert np.all(W1g[j][m < j + 1] == 0)
+
+
+# --------------------------------------------------------------- sampling
+
+@pytest.mark.parametrize("n,h,act", [(40, 60, oracle.RELU), (40, 17, oracle.SIGMOID), (25, 25, oracle.RELU)])
+def test_literal_and_incremental_samplers_agree(n, h, act):
+    """Algorithm 1 taken literally and its incremental form give the same
+    samples on shared uniforms (barring near-ties) and the same log pi."""
+    P = _params(n, h, 19)
+    U = inputs.uniforms(48, n, 20)
+    S1, lp1 = oracle.sample(P, U, act, literal=True)
+    S2, lp2 = oracle.sample(P, U, act, literal=False)
+    Z = oracle.logits(P, S1, act)
+    near = np.abs(U.astype(np.float64) - 1 / (1 + np.exp(-Z))) < 1e-12
+    rows = ~near.any(axis=1)
+    assert rows.sum() >= 40
+    assert np.array_equal(S1[rows], S2[rows])
+    assert np.allclose(lp1, oracle.logprob(P, S1, act), rtol=0, atol=1e-10)
+    assert np.allclose(lp2, oracle.logprob(P, S2, act), rtol=0, atol=1e-10)
+
+
+def test_sampler_teacher_forced_rule():
+    """Each drawn spin is +1 exactly when u < pi_i(+1 | s_<i) on its own prefix."""
+    n, h = 50, 70
+    P = _params(n, h, 21)
+    U = inputs.uniforms(32, n, 22)
+    S, _ = oracle.sample(P, U)
+    p = 1 / (1 + np.exp(-oracle.logits(P, S)))
+    assert np.array_equal(S == 1, U.astype(np.float64) < p)
+
+
+def test_sampler_is_exact_chi_square():
+    """Empirical frequencies of 2^n states match pi(s) (exact sampling claim
+    of Sec. 2.3 / Sec. 4), chi-square at n = 5."""
+    n, h = 5, 9
+    P = _params(n, h, 23, scale=2.0)
+    N = 60000
+    U = inputs.uniforms(N, n, 24)
+    S, _ = oracle.sample(P, U)
+    idx = ((S == -1).astype(np.int64) << np.arange(n)).sum(axis=1)
+    counts = np.bincount(idx, minlength=1 << n)
+    states = np.array([[1 - 2 * ((x >> i) & 1) for i in range(n)] for x in range(1 << n)], dtype=np.int8)
+    p = np.exp(oracle.logprob(P, states))
+    assert abs(p.sum() - 1) < 1e-12
+    exp_c = N * p
+    chi2 = ((counts - exp_c) ** 2 / exp_c).sum()
+    from scipy.stats import chi2 as chi2d
+    assert chi2d.sf(chi2, (1 << n) - 1) > 1e-3, chi2
