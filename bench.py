@@ -1,0 +1,354 @@
+"""Benchmark of one VQMC iteration (Sec. 2.1, 2.3, 4 of arXiv 2106.13308) on GB300.
+
+A step is one full iteration through the C ABI (vqmc_step): exact samples from
+the MADE model (persistent sampler), diagonal Max-Cut local energies, FP64
+statistics, the score-function gradient (log-prob forward + adjoint GEMMs) and
+one Adam update.  Workload: Max-Cut on G(n = 10000, p = 8/9999) with weights
+uniform in {1..10}, MADE with h = 2000 ReLU units, B = 2048 samples per step.
+
+The headline value is the BF16+FP32 path (BF16 weights, FP32 accumulation and
+sampler, FP64 statistics); the plain FP32 path is measured in the same run
+and reported under "fp32".  Under torchrun with N > 1 every rank runs an
+independent replica (the path has no collective on one GPU per rank); the
+value is the sum over ranks of iterations / max rank time.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (a
+bounded sub-batch per step, scaled linearly to the full batch).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "VQMC iterations/s and exact samples/s at N=10,000 (BF16+FP32 vs plain FP32, 1 GB300)"
+UNIT = "it/s"
+WORKLOAD = "maxcut_er10000"
+FP32_FMA_LANES_PER_SM = 128
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _workload(name):
+    from paper_2106_13308_gb300 import inputs
+    cfg = inputs.config(name)
+    inst = inputs.make_instance(cfg)
+    return cfg, inst
+
+
+def _config_json(cfg, inst, world, precision_note):
+    nnz = int(len(inst["col"])) if inst["kind"] != "dense" else cfg["n"] * (cfg["n"] - 1) // 2
+    return {
+        "workload": f"{cfg['name']}: Max-Cut on Erdos-Renyi G(n={cfg['n']}, p=8/9999), {nnz} edges, "
+                    f"weights uniform in {{1..10}} (int32 CSR); MADE h={cfg['h']} {cfg['act']}; "
+                    f"batch {cfg['B']} exact samples per step; Adam lr 1e-2",
+        "n": cfg["n"], "h": cfg["h"], "batch": cfg["B"], "edges": nnz,
+        "precision": precision_note,
+        "l2": "no flush: one step streams > 1 GB (theta, Adam state, weight copies), far above the 129 MB L2",
+        "parallelism": f"replicas x{world}",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while active."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def _make(cfg, inst, precision):
+    import torch
+    from paper_2106_13308_gb300 import inputs
+    from paper_2106_13308_gb300.vqmc import VQMC
+    m = VQMC(cfg["n"], cfg["h"], cfg["B"], inst, act=cfg["act"], precision=precision, seed=12345)
+    theta = inputs.made_params(cfg["n"], cfg["h"], cfg["param_seed"], w_std=cfg["w_std"])
+    m.set_params(torch.from_numpy(theta))
+    return m
+
+
+def _timed_steps(m, B, K, W, dist_on):
+    """Device time of K steps (CUDA events on the launching stream), after W
+    warm-up steps, bracketed by barrier + synchronize; per-part times from the
+    library's own events inside the same region."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(W):
+        m.step(B)
+    torch.cuda.synchronize()
+    m.timing_enable(True)
+    if dist_on:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        m.step(B)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist_on:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    parts, steps, launches = m.timing_read()
+    m.timing_enable(False)
+    return ms, parts, steps, launches
+
+
+def _e2e(m, B, K, W):
+    """Same metric through the public Python API as a user runs it: every step
+    reads the statistics and the batch's energies back to pinned host memory."""
+    import torch
+    from paper_2106_13308_gb300.vqmc import StepStats
+    import ctypes
+    host_e = torch.empty(B, dtype=m.e_dtype).pin_memory()
+    stats_buf = torch.empty(ctypes.sizeof(StepStats), dtype=torch.uint8).pin_memory()
+    out = StepStats.from_address(stats_buf.data_ptr())
+    for _ in range(W):
+        m.step(B, out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        m.step(B, out)
+        _, e = m.last_batch(B)
+        host_e.copy_(e, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        _ = out.mean + float(host_e[0])
+    t = time.perf_counter() - t0
+    return K / t, ctypes.sizeof(StepStats) + B * 4
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def _oracle_iteration(cfg, inst, Bsub, theta, it):
+    import numpy as np
+    import oracle
+    n, h = cfg["n"], cfg["h"]
+    P = oracle.theta_to_made(theta, n, h)
+    U = oracle.uniforms(Bsub, n, 12345, it)
+    act = oracle.RELU if cfg["act"] == "relu" else oracle.SIGMOID
+    S, _ = oracle.sample(P, U, act)
+    (dW1, db1, dW2, db2), st, E = oracle.vqmc_grad(P, inst, S, act)
+    g = oracle.made_to_theta(dW1, db1, dW2, db2)
+    t = theta.astype(np.float64)
+    oracle.adam(t, np.zeros_like(t), np.zeros_like(t), g, 1)
+    return st
+
+
+def _cpu_baseline(cfg, inst, target_s=12.0, max_sub=None):
+    """The oracle, as it stands, on a bounded sub-batch of one step."""
+    import oracle
+    from paper_2106_13308_gb300 import inputs
+    oracle.build()
+    cores = oracle.num_threads()
+    theta = inputs.made_params(cfg["n"], cfg["h"], cfg["param_seed"], w_std=cfg["w_std"])
+    Bsub = max(cores, 1)
+    t0 = time.perf_counter()
+    _oracle_iteration(cfg, inst, Bsub, theta, 0)
+    t = time.perf_counter() - t0
+    if t < target_s / 3:
+        Bsub = int(min(cfg["B"], max_sub or cfg["B"], max(Bsub, Bsub * target_s / max(t, 1e-3))) // cores * cores)
+        Bsub = max(Bsub, cores)
+        t0 = time.perf_counter()
+        _oracle_iteration(cfg, inst, Bsub, theta, 1)
+        t = time.perf_counter() - t0
+    per_sample = t / Bsub
+    it_s = 1.0 / (per_sample * cfg["B"])
+    return {"value": it_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "samples_per_s": Bsub / t,
+            "sample": f"one full oracle iteration (incremental FP64 sampler, energies, FP64 stats, "
+                      f"chain-rule gradient, Adam) on {Bsub} of the {cfg['B']} samples of {cfg['name']}, "
+                      f"{t:.1f} s wall, scaled linearly to the full batch"}
+
+
+# -------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default=WORKLOAD)
+    ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 arm")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    rank, world, local = _dist_env()
+    W = max(args.warmup, 3)
+    K = args.steps
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cfg, inst = _workload(args.config)
+        import oracle
+        from paper_2106_13308_gb300 import inputs
+        oracle.build()
+        cores = oracle.num_threads()
+        theta = inputs.made_params(cfg["n"], cfg["h"], cfg["param_seed"], w_std=cfg["w_std"])
+        # size one step's sub-batch so that W + K steps take about two minutes
+        t0 = time.perf_counter()
+        _oracle_iteration(cfg, inst, cores, theta, 0)
+        per_sample = (time.perf_counter() - t0) / cores
+        budget = 120.0 / (W + K)
+        Bsub = int(max(cores, min(cfg["B"], budget / per_sample)) // cores * cores) or cores
+        times = []
+        for k in range(W + K):
+            t0 = time.perf_counter()
+            _oracle_iteration(cfg, inst, Bsub, theta, k)
+            if k >= W:
+                times.append(time.perf_counter() - t0)
+        per_step = statistics.mean(times) * cfg["B"] / Bsub
+        v = 1.0 / per_step
+        base = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"each step: one full oracle iteration on {Bsub} of the {cfg['B']} samples of "
+                          f"{cfg['name']}, scaled linearly to the full batch"}
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": W, "ms_per_step": 1000.0 * per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": _config_json(cfg, inst, 1, "FP64 CPU oracle"),
+                "cpu_baseline": base,
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    dist_on = world > 1
+    if dist_on:
+        torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    cfg, inst = _workload(args.config)
+    B = cfg["B"]
+
+    m = _make(cfg, inst, "bf16")
+    clocks = ClockSampler(local)
+    # warm-up outside the clock window, then the timed region with clocks sampled
+    for _ in range(W):
+        m.step(B)
+    torch.cuda.synchronize()
+    clocks.start()
+    ms, parts, steps, launches = _timed_steps(m, B, K, 0, dist_on)
+    clk = clocks.stop()
+    if dist_on:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / K
+    value = world * K / (ms / 1000.0)
+    flags = m.check()
+
+    # dominant kernel: the persistent sampler (FP32 FMA pipe)
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = sm_count * FP32_FMA_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
+    sample_ms = parts["sample"] / max(steps, 1)
+    flops = 2.0 * cfg["h"] * cfg["n"] * B
+    achieved = flops / (sample_ms / 1000.0) / 1e12
+    roofline = {"bound": "alu", "kernel": "sampler_kernel (FP32 FMA pipe)", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {peak_mhz:.0f} MHz (fallback: no "
+                               "measured FP32 peak)",
+                "algorithmic": f"2*h*n*B = {flops:.3e} flop per launch (h*n FMA per sample)"}
+    part_ms = {k: v / max(steps, 1) for k, v in parts.items()}
+
+    e2e_v, d2h = _e2e(m, B, max(3, K // 2), 2)
+    e2e_v *= world
+
+    fp32 = None
+    if not args.no_fp32:
+        del m
+        torch.cuda.empty_cache()
+        m32 = _make(cfg, inst, "fp32")
+        ms32, parts32, steps32, _ = _timed_steps(m32, B, max(3, K // 2), W, dist_on)
+        k32 = max(3, K // 2)
+        fp32 = {"value": world * k32 / (ms32 / 1000.0), "unit": UNIT, "ms_per_step": ms32 / k32,
+                "samples_per_s": world * k32 * B / (ms32 / 1000.0),
+                "part_ms": {k: v / max(steps32, 1) for k, v in parts32.items()}}
+        del m32
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = _cpu_baseline(cfg, inst)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16", "data": "synthetic",
+                "config": _config_json(cfg, inst, world, "BF16 weights, FP32 accumulation and sampler, FP64 stats"),
+                "samples_per_s": value * B, "part_ms": part_ms, "fp32": fp32,
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clk, "device_error_flags": flags}
+        print(json.dumps(line), flush=True)
+    if dist_on:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,262 @@
+/*
+ * vqmc.h -- C ABI of the GB300 (sm_103a) VQMC hot-path library.
+ *
+ * One variational iteration of "Overcoming barriers to scalability in
+ * variational quantum Monte Carlo" (arXiv 2106.13308) on one GPU:
+ *
+ *   1. draw B exact samples s ~ pi_theta from a MADE autoregressive model
+ *      (Sec. 2.3, Algorithm 1),
+ *   2. evaluate log pi_theta(s)                               (Sec. 2.3),
+ *   3. evaluate the diagonal Ising local energy
+ *      E(s) = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i          (Sec. 2.4),
+ *   4. form the FP64 batch statistics and the score-function gradient
+ *      g = sum_b (E_b - mean E)/B * grad log pi(s_b)          (Sec. 2.1),
+ *   5. apply one Adam step (the paper's default optimiser, Sec. 5.1).
+ *
+ * Model.  n spins s_i in {-1,+1}, h hidden units, one masked hidden layer:
+ *   a = (M1 . W1) s + b1,  g1 = act(a),  z = (M2 . W2) g1 + b2,
+ *   pi_i(s_i = +1 | s_<i) = sigma(z_i),  log pi(s) = sum_i log sigma(s_i z_i).
+ * Hidden unit k (0-based) has degree m(k) = 1 + floor(k (n-1) / h);
+ * M1[k][j] = [m(k) >= j], M2[i][k] = [i > m(k)] with 1-based i, j.
+ * act is the rectifier (the paper's choice) or the logistic sigmoid.
+ *
+ * Parameter layout (d = 2hn + h + n entries, Sec. 4), float32:
+ *   theta = [ W1^T (n x h, row j = input j) | b1 (h) | W2 (n x h) | b2 (n) ].
+ * Entries outside the masks are held at exactly zero by the library.
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are device pointers owned by the caller; the library
+ *     never frees them.  Pointers named h_* are host pointers.
+ *   - Arrays are dense and row-major: spins int8 [B][n] with values +-1,
+ *     uniforms float32 [B][n], energies int32 or float32 [B], log-probs
+ *     float32 [B], gradients float32 [d] in the theta layout.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls only
+ *     enqueue work and return; they never synchronise the device except
+ *     where stated (vqmc_create, vqmc_set_params/get_params with host
+ *     pointers, vqmc_check, vqmc_save/load).  Calls that share one context
+ *     use its workspaces and must not run concurrently on different streams.
+ *   - B must satisfy 0 <= B <= config.max_batch; B = 0 is a no-op.
+ *   - Every call returns a vqmc_status; on failure vqmc_last_error() gives a
+ *     thread-local message.  Device-side faults that a kernel can detect
+ *     (a bounded wait that ran out, a non-finite energy) set bits in a sticky
+ *     device error word that vqmc_check() reads and clears.
+ */
+#ifndef VQMC_H_
+#define VQMC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vqmc_ctx vqmc_ctx;
+typedef void* vqmc_stream; /* cudaStream_t */
+
+typedef enum {
+  VQMC_OK = 0,
+  VQMC_ERR_INVALID_ARG = 1, /* bad pointer, size or enum value */
+  VQMC_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  VQMC_ERR_OOM = 3,         /* device allocation failed */
+  VQMC_ERR_NONFINITE = 4,   /* a NaN/Inf energy or statistic was produced */
+  VQMC_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  VQMC_ERR_UNSUPPORTED = 6  /* size or option this build does not handle */
+} vqmc_status;
+
+enum { VQMC_ACT_RELU = 0, VQMC_ACT_SIGMOID = 1 };
+
+/* Precision of the model weights inside the kernels.  FP32: FP32 weights
+ * and FP32 CUDA-core GEMMs.  BF16: BF16 copies of W1, W2 (rounded to nearest
+ * even from the FP32 master after every update) with FP32 accumulation; the
+ * sampler still accumulates in FP32; the log-prob/backward GEMMs run on the
+ * tcgen05 tensor cores with BF16 operands.  The master theta, Adam state and
+ * gradients are FP32 in both modes; batch statistics are FP64. */
+enum { VQMC_PREC_FP32 = 0, VQMC_PREC_BF16 = 1 };
+
+/* Hamiltonian storage. */
+enum {
+  VQMC_HAM_SPARSE_I32 = 0, /* CSR strict upper triangle, int32 weights; E is int32, exact */
+  VQMC_HAM_SPARSE_F32 = 1, /* CSR strict upper triangle, float32 weights; E is float32 */
+  VQMC_HAM_DENSE_F32 = 2   /* dense symmetric float32 J (zero diagonal); E is float32 */
+};
+
+/* Device error word bits (vqmc_check). */
+enum {
+  VQMC_DEVERR_TIMEOUT = 1u,   /* a bounded mbarrier/flag wait gave up */
+  VQMC_DEVERR_NONFINITE = 2u  /* a non-finite energy or statistic */
+};
+
+typedef struct {
+  int32_t n;          /* number of spins, >= 1 */
+  int32_t h;          /* hidden units, >= 1 */
+  int32_t max_batch;  /* largest B any call will pass, >= 1 */
+  int32_t act;        /* VQMC_ACT_* */
+  int32_t precision;  /* VQMC_PREC_* */
+  float lr;           /* Adam learning rate (paper default 1e-2) */
+  float beta1;        /* Adam beta1 (0.9) */
+  float beta2;        /* Adam beta2 (0.999) */
+  float eps;          /* Adam epsilon (1e-8) */
+  uint32_t reserved;
+  uint64_t seed;      /* Philox4x32-10 key for the internal uniforms */
+} vqmc_config;
+
+/* Problem instance, host memory, copied to the device by vqmc_create.
+ * Sparse kinds: row_ptr int32 [n+1], col int32 [nnz] with col > row (the
+ * strict upper triangle, each undirected edge once), w [nnz] int32 or float32
+ * per kind.  Dense kind: J float32 [n][n] symmetric with zero diagonal.
+ * field: h_i, [n] of the weight type (int32 for SPARSE_I32, float32
+ * otherwise), or NULL for h = 0. */
+typedef struct {
+  int32_t kind; /* VQMC_HAM_* */
+  int32_t n;
+  int32_t nnz;
+  int32_t reserved;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const void* w;
+  const void* field;
+  const float* J;
+} vqmc_instance;
+
+/* Result of one vqmc_step, FP64 statistics of the batch's local energies
+ * (Eq. (e:vmc) and Eq. (eq:stochastic_variance) estimated on the batch). */
+typedef struct {
+  double mean;          /* L = sum_b E_b / B */
+  double var;           /* sum_b (E_b - L)^2 / B */
+  double min;           /* lowest energy in the batch */
+  double max;           /* highest energy in the batch */
+  uint64_t iteration;   /* Philox iteration counter used for this step */
+  uint32_t error_flags; /* snapshot of the device error word (VQMC_DEVERR_*) */
+  uint32_t reserved;
+} vqmc_step_stats;
+
+/* Creates a context: validates cfg/inst, allocates the FP32 master theta
+ * (zero), Adam state, BF16/FP32 weight copies and every workspace for up to
+ * cfg->max_batch samples, and copies the instance to the device.  Synchronous.
+ * Errors: INVALID_ARG (n, h, max_batch < 1, inst->n != cfg->n, bad kind or
+ * NULL arrays), OOM, CUDA, UNSUPPORTED (sizes this build cannot tile). */
+vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_ctx** out);
+
+/* Frees everything the context owns.  NULL is accepted. */
+void vqmc_destroy(vqmc_ctx* ctx);
+
+/* d = 2hn + h + n. */
+int64_t vqmc_num_params(const vqmc_ctx* ctx);
+
+/* Replaces theta (d floats, host or device per theta_on_device), zeroes the
+ * entries outside the MADE masks, resets the Adam moments and step count and
+ * refreshes the kernels' weight copies.  Synchronous when theta is on the
+ * host.  Errors: INVALID_ARG, CUDA. */
+vqmc_status vqmc_set_params(vqmc_ctx* ctx, const float* theta, int theta_on_device, vqmc_stream stream);
+
+/* Copies the FP32 master theta out (d floats). */
+vqmc_status vqmc_get_params(vqmc_ctx* ctx, float* theta, int theta_on_device, vqmc_stream stream);
+
+/* Device pointer to the context's FP32 master theta (d floats, owned by the
+ * context).  After writing to it, call vqmc_params_updated. */
+float* vqmc_params_device(vqmc_ctx* ctx);
+
+/* Re-applies the masks and refreshes the weight copies after theta was
+ * written through vqmc_params_device (does not touch the Adam state). */
+vqmc_status vqmc_params_updated(vqmc_ctx* ctx, vqmc_stream stream);
+
+/* Writes the uniforms the sampler draws internally for Philox iteration
+ * `iteration`: d_u[b][i] = word (i mod 4) of
+ * Philox4x32-10(counter = (i/4, b, iteration_lo, iteration_hi), key = seed)
+ * mapped to [0,1) as (x >> 8) * 2^-24.  d_u: float32 [B][n]. */
+vqmc_status vqmc_uniforms(vqmc_ctx* ctx, int32_t B, uint64_t iteration, float* d_u, vqmc_stream stream);
+
+/* Algorithm 1 (Sec. 2.3): draws B exact samples.  Spin i of sample b is +1
+ * iff u_{b,i} < sigma(z_i(s_<i)), else -1, with u = d_u[b][i] when d_u is not
+ * NULL, else the internal Philox uniforms of `iteration` (see vqmc_uniforms).
+ * Writes d_s int8 [B][n] and, if d_logp is not NULL, log pi(s_b) float32 [B]
+ * accumulated in FP32 while sampling.  The conditionals are computed in FP32
+ * from the FP32 or BF16 weight copies (per precision). */
+vqmc_status vqmc_sample(vqmc_ctx* ctx, int32_t B, const float* d_u, uint64_t iteration, int8_t* d_s,
+                        float* d_logp, vqmc_stream stream);
+
+/* Diagonal local energy l(s) = H_ss (Sec. 2.1, Sec. 2.4) of B configurations
+ * d_s int8 [B][n]: E_b = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i.  d_e is
+ * int32 [B] (exact) for VQMC_HAM_SPARSE_I32 and float32 [B] otherwise.  The
+ * dense kind runs S.J on the tensor cores in BF16 with a hi/lo split of J
+ * (error stated in the design notes) in BF16 precision, FP32 otherwise. */
+vqmc_status vqmc_local_energy(vqmc_ctx* ctx, int32_t B, const int8_t* d_s, void* d_e, vqmc_stream stream);
+
+/* log pi(s_b) (Sec. 2.3) of B configurations by the full masked forward
+ * pass (two masked GEMMs).  d_logp float32 [B]. */
+vqmc_status vqmc_logprob(vqmc_ctx* ctx, int32_t B, const int8_t* d_s, float* d_logp, vqmc_stream stream);
+
+/* Adjoint of vqmc_logprob: d_grad[d] = sum_b d_gout[b] * grad_theta log pi(s_b)
+ * (overwrites d_grad).  Hidden activations are recomputed, not taken from a
+ * previous forward.  Entries outside the masks are written as 0. */
+vqmc_status vqmc_logprob_backward(vqmc_ctx* ctx, int32_t B, const int8_t* d_s, const float* d_gout,
+                                  float* d_grad, vqmc_stream stream);
+
+/* FP64 batch statistics of energies d_e (int32 or float32 per instance kind):
+ * d_stats double [4] = {mean, var, min, max} (var with 1/B), and, if d_coef
+ * is not NULL, the score-function coefficients c_b = (E_b - mean)/B as
+ * float32 [B].  A non-finite value sets VQMC_DEVERR_NONFINITE. */
+vqmc_status vqmc_energy_stats(vqmc_ctx* ctx, int32_t B, const void* d_e, double* d_stats, float* d_coef,
+                              vqmc_stream stream);
+
+/* Score-function gradient of one batch (Sec. 2.1):
+ * d_grad = sum_b (E_b - mean)/B * grad log pi(s_b); d_stats as above
+ * (may be NULL). */
+vqmc_status vqmc_grad(vqmc_ctx* ctx, int32_t B, const int8_t* d_s, const void* d_e, float* d_grad,
+                      double* d_stats, vqmc_stream stream);
+
+/* One Adam step on the master theta with gradient d_grad[d], then refreshes
+ * the weight copies.  Increments the context's Adam step count. */
+vqmc_status vqmc_adam(vqmc_ctx* ctx, const float* d_grad, vqmc_stream stream);
+
+/* One full VQMC iteration: sample B configurations with the internal
+ * uniforms of the context's iteration counter, local energies, FP64
+ * statistics, score-function gradient and one Adam step; then increments the
+ * iteration counter.  If h_out is not NULL it receives the step's statistics
+ * by an asynchronous device-to-host copy on `stream` (synchronise before
+ * reading; use pinned memory for a truly asynchronous copy). */
+vqmc_status vqmc_step(vqmc_ctx* ctx, int32_t B, vqmc_stream stream, vqmc_step_stats* h_out);
+
+/* Device pointers to the last vqmc_step's samples (int8 [B][n]) and energies
+ * (int32/float32 [B]); owned by the context, overwritten by the next step. */
+vqmc_status vqmc_last_batch(vqmc_ctx* ctx, const int8_t** d_s, const void** d_e);
+
+/* Current Philox iteration counter and Adam step count. */
+uint64_t vqmc_iteration(const vqmc_ctx* ctx);
+
+/* Synchronises the device, reads and clears the sticky device error word.
+ * Returns TIMEOUT or NONFINITE if the corresponding bit was set. */
+vqmc_status vqmc_check(vqmc_ctx* ctx, uint32_t* flags_out);
+
+/* Checkpoint: writes/reads theta, Adam moments, Adam step count, the Philox
+ * seed and iteration counter and a hash of (n, h, act, instance) to/from a
+ * binary file.  vqmc_load fails with INVALID_ARG on a shape/instance
+ * mismatch.  Synchronous. */
+vqmc_status vqmc_save(vqmc_ctx* ctx, const char* path);
+vqmc_status vqmc_load(vqmc_ctx* ctx, const char* path);
+
+/* Per-part timing of vqmc_step.  While enabled, every vqmc_step records CUDA
+ * events on its stream between its parts (no synchronisation), for up to
+ * 4096 steps.  vqmc_timing_read synchronises, and returns the summed device
+ * time of each part over the recorded steps in ms_out[VQMC_NUM_PARTS], the
+ * number of recorded steps and the number of kernels those steps launched.
+ * Enabling resets the record. */
+enum {
+  VQMC_PART_SAMPLE = 0,   /* persistent sampler (uniforms generated in-kernel) */
+  VQMC_PART_ENERGY = 1,   /* local energies */
+  VQMC_PART_STATS = 2,    /* FP64 statistics and coefficients */
+  VQMC_PART_GRAD = 3,     /* log-prob forward + adjoint GEMMs and reductions */
+  VQMC_PART_ADAM = 4,     /* Adam step and weight-copy refresh */
+  VQMC_NUM_PARTS = 5
+};
+vqmc_status vqmc_timing_enable(vqmc_ctx* ctx, int enable);
+vqmc_status vqmc_timing_read(vqmc_ctx* ctx, double* ms_out, int64_t* steps_out, int64_t* launches_out);
+
+/* Thread-local description of the last error. */
+const char* vqmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VQMC_H_ */

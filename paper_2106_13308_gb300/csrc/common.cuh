@@ -1,0 +1,147 @@
+// Internal declarations shared by the CUDA translation units of libvqmc.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "vqmc.h"
+
+namespace vqmc {
+
+using bf16 = __nv_bfloat16;
+
+// Leading dimensions of every kernel-side matrix are padded to this many
+// elements, so rows start on 128-byte boundaries (bulk/TMA copies need 16).
+constexpr int kPad = 64;
+inline int pad_up(int x, int p = kPad) { return (x + p - 1) / p * p; }
+
+// MADE degree of hidden unit k (0-based): m(k) = 1 + floor(k (n-1) / h).
+__host__ __device__ inline int degree(int k, int n, int h) {
+  return 1 + (int)(((long long)k * (long long)(n - 1)) / (long long)h);
+}
+
+// Number of hidden units whose degree is <= x, i.e. #{k : k (n-1) < x h}.
+__host__ __device__ inline int count_deg_le(int x, int n, int h) {
+  if (x < 1) return 0;
+  if (n <= 1) return h;
+  long long c = ((long long)x * h + (n - 2)) / (n - 1);
+  return c > h ? h : (int)c;
+}
+
+// Device error word bits mirror VQMC_DEVERR_*.
+constexpr uint32_t kErrTimeout = VQMC_DEVERR_TIMEOUT;
+constexpr uint32_t kErrNonfinite = VQMC_DEVERR_NONFINITE;
+
+// Bound on every device-side spin wait (try_wait iterations; each try_wait
+// may itself suspend the thread for a hardware-chosen interval).
+constexpr long long kSpinLimit = 1ll << 26;
+
+}  // namespace vqmc
+
+// The context behind the opaque handle of vqmc.h.
+struct vqmc_ctx {
+  vqmc_config cfg;
+  int n, h, Bmax;
+  int np, hp, Bp;  // padded n, h, batch
+  int act, prec;   // VQMC_ACT_*, VQMC_PREC_*
+  int ham;         // VQMC_HAM_*
+  int nnz;
+  int64_t d;
+  uint64_t inst_hash = 0;
+  int device;
+  int num_sms;
+
+  // FP32 master parameters, optimiser state, gradient (d floats each)
+  float* theta = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  float* grad = nullptr;
+  int64_t adam_t = 0;
+  uint64_t iter = 0;
+
+  // Kernel-side weight copies, element type float (FP32) or bf16 (BF16):
+  //   wt_s [n][hp]  rows of W1^T (input j -> all units), sampler
+  //   v_s  [n][hp]  rows of W2 (output i <- all units), sampler and Z GEMM
+  //   w_s  [h][np]  rows of W1 (unit k <- all inputs), hidden GEMM
+  //   vt_s [h][np]  rows of W2^T (unit k -> all outputs), backward GEMM
+  void* wt_s = nullptr;
+  void* v_s = nullptr;
+  void* w_s = nullptr;
+  void* vt_s = nullptr;
+  float* b1 = nullptr;  // aliases into theta
+  float* b2 = nullptr;
+
+  // instance
+  int32_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  void* w = nullptr;      // int32 or float [nnz]
+  void* field = nullptr;  // int32 or float [n] or null
+  float* J = nullptr;     // dense [n][np] float
+  void* J_hi = nullptr;   // dense split, [n][np] bf16
+  void* J_lo = nullptr;
+
+  // workspaces (element type per precision unless noted)
+  int8_t* S = nullptr;     // int8 [Bmax][n] samples of vqmc_step
+  void* E = nullptr;       // int32/float [Bmax]
+  void* Sx = nullptr;      // [Bmax][np] spins as GEMM operand
+  void* St = nullptr;      // [n][Bp] spins transposed
+  void* H = nullptr;       // [Bmax][hp] hidden activations
+  void* Ht = nullptr;      // [h][Bp]
+  void* D = nullptr;       // [Bmax][np] output adjoint delta
+  void* Dt = nullptr;      // [n][Bp]
+  void* GAt = nullptr;     // [h][Bp] hidden pre-activation adjoint, transposed
+  float* logp = nullptr;   // [Bmax]
+  float* coef = nullptr;   // [Bmax]
+  double* stats = nullptr; // [4]
+  float* row_part = nullptr;  // [ceil(max(n,h)/128)][Bmax] partial row sums
+  float* col_part = nullptr;  // [ceil(Bmax/128)][max(np,hp)] partial column sums
+  int row_part_ld = 0, col_part_ld = 0, row_part_tiles = 0, col_part_tiles = 0;
+  uint32_t* err = nullptr;   // sticky device error word
+  // per-part step timing (vqmc_timing_*): events[step][part boundary]
+  bool timing = false;
+  int64_t timed_steps = 0;
+  int64_t launches = 0;
+  cudaEvent_t* events = nullptr;  // kMaxTimedSteps * (VQMC_NUM_PARTS + 1)
+  vqmc_step_stats* step_stats = nullptr;  // device copy of the last step's stats
+};
+
+namespace vqmc {
+
+// ---- sampler.cu
+cudaError_t launch_uniforms(int B, int n, uint64_t seed, uint64_t iteration, float* d_u, cudaStream_t st);
+cudaError_t launch_sampler(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,
+                           float* d_logp, void* Sx, void* St, cudaStream_t st);
+
+// ---- eloc.cu
+cudaError_t launch_eloc_sparse(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st);
+cudaError_t launch_eloc_dense_finish(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st);
+cudaError_t launch_stats(const vqmc_ctx* c, int B, const void* d_e, double* d_stats, float* d_coef,
+                         cudaStream_t st);
+cudaError_t launch_spins_to_operands(const vqmc_ctx* c, int B, const int8_t* d_s, void* Sx, void* St,
+                                     cudaStream_t st);
+cudaError_t launch_row_sum(const vqmc_ctx* c, int B, int ntiles, float* out, cudaStream_t st);
+cudaError_t launch_col_sum(const vqmc_ctx* c, int N, int mtiles, float* out, cudaStream_t st);
+
+// ---- gemm (gemm_simt.cu, gemm_tc.cu): the five masked GEMMs of the forward
+// and adjoint passes plus the dense local-energy GEMM.  Operand and output
+// layouts are fixed by the context (see vqmc_api.cu).
+enum GemmOp {
+  kOpHidden = 0,  // H = act(S W1^T + b1); writes H, Ht
+  kOpOut = 1,     // Z = H W2^T + b2; logp row partials; if coef: delta, Dt, dc partials
+  kOpDV = 2,      // dW2 = Dt . Ht^T  (masked) -> grad
+  kOpGA = 3,      // G = D . W2 ; GA = G * act'(H) -> GAt ; db1 partials
+  kOpDW = 4,      // dW1^T = St . GAt^T (masked) -> grad
+  kOpEloc = 5     // T = S J (hi/lo) ; row partials 1/2 s.T
+};
+cudaError_t launch_gemm(const vqmc_ctx* c, GemmOp op, int B, const int8_t* d_s, const float* coef,
+                        float* grad, cudaStream_t st);
+
+// ---- adam.cu
+cudaError_t launch_mask_params(vqmc_ctx* c, cudaStream_t st);
+cudaError_t launch_refresh_weights(vqmc_ctx* c, cudaStream_t st);
+cudaError_t launch_adam(vqmc_ctx* c, const float* d_grad, cudaStream_t st);
+cudaError_t launch_dense_split(vqmc_ctx* c, cudaStream_t st);
+
+}  // namespace vqmc

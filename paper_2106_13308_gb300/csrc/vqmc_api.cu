@@ -1,0 +1,617 @@
+// C ABI of libvqmc (include/vqmc.h): context management and the VQMC
+// iteration of the paper (Sec. 2.1, 2.3, 4, 5.1) as a sequence of kernels on
+// one stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "gemm.cuh"
+
+using namespace vqmc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+vqmc_status fail(vqmc_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define VQ_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(e_ == cudaErrorMemoryAllocation ? VQMC_ERR_OOM                               \
+                  : e_ == cudaErrorNotSupported   ? VQMC_ERR_UNSUPPORTED                       \
+                                                  : VQMC_ERR_CUDA,                             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+  } while (0)
+
+template <typename P>
+cudaError_t dalloc(P** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaMemset(*p, 0, bytes);
+}
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t bytes) {
+  const unsigned char* c = (const unsigned char*)p;
+  for (size_t i = 0; i < bytes; ++i) h = (h ^ c[i]) * 1099511628211ull;
+  return h;
+}
+
+constexpr int64_t kMaxTimedSteps = 4096;
+
+size_t esize(const vqmc_ctx* c) { return c->prec == VQMC_PREC_BF16 ? 2 : 4; }
+
+cudaStream_t S(vqmc_stream s) { return (cudaStream_t)s; }
+
+vqmc_status check_B(const vqmc_ctx* c, int B) {
+  if (!c) return fail(VQMC_ERR_INVALID_ARG, "null context");
+  if (B < 0 || B > c->Bmax) return fail(VQMC_ERR_INVALID_ARG, "batch size outside [0, max_batch]");
+  return VQMC_OK;
+}
+
+// ---- GEMM dispatch ---------------------------------------------------------
+
+template <typename T>
+GemmArgs<T> make_args(const vqmc_ctx* c, GemmOp op, int B, const int8_t* d_s, const float* coef, float* grad) {
+  GemmArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.op = op;
+  a.n = c->n;
+  a.h = c->h;
+  a.act = c->act;
+  a.ldr = c->row_part_ld;
+  a.ldc = c->col_part_ld;
+  const int n = c->n, h = c->h;
+  switch (op) {
+    case kOpHidden:
+      a.M = B, a.N = h, a.K = n;
+      a.A = (const T*)c->Sx, a.lda = c->np;
+      a.Bm = (const T*)c->w_s, a.ldb = c->np;
+      a.bias = c->b1;
+      a.out = (T*)c->H, a.ldo = c->hp;
+      a.out_t = (T*)c->Ht, a.ldt = c->Bp;
+      break;
+    case kOpOut:
+      a.M = B, a.N = n, a.K = h;
+      a.A = (const T*)c->H, a.lda = c->hp;
+      a.Bm = (const T*)c->v_s, a.ldb = c->hp;
+      a.bias = c->b2;
+      a.S8 = d_s, a.lds8 = n;
+      a.coef = coef;
+      a.out = (T*)c->D, a.ldo = c->np;
+      a.out_t = (T*)c->Dt, a.ldt = c->Bp;
+      a.row_part = c->row_part;
+      a.col_part = coef ? c->col_part : nullptr;
+      break;
+    case kOpDV:
+      a.M = n, a.N = h, a.K = B;
+      a.A = (const T*)c->Dt, a.lda = c->Bp;
+      a.Bm = (const T*)c->Ht, a.ldb = c->Bp;
+      a.gout = grad + (size_t)n * h + h, a.ldg = h;
+      break;
+    case kOpGA:
+      a.M = B, a.N = h, a.K = n;
+      a.A = (const T*)c->D, a.lda = c->np;
+      a.Bm = (const T*)c->vt_s, a.ldb = c->np;
+      a.aux = (const T*)c->H, a.ldaux = c->hp;
+      a.out_t = (T*)c->GAt, a.ldt = c->Bp;
+      a.col_part = c->col_part;
+      break;
+    case kOpDW:
+      a.M = n, a.N = h, a.K = B;
+      a.A = (const T*)c->St, a.lda = c->Bp;
+      a.Bm = (const T*)c->GAt, a.ldb = c->Bp;
+      a.gout = grad, a.ldg = h;
+      break;
+    case kOpEloc:
+      a.M = B, a.N = n, a.K = n;
+      a.A = (const T*)c->Sx, a.lda = c->np;
+      a.ldb = c->np;
+      a.S8 = d_s, a.lds8 = n;
+      a.row_part = c->row_part;
+      break;
+  }
+  return a;
+}
+
+}  // namespace
+
+namespace vqmc {
+
+cudaError_t launch_gemm(const vqmc_ctx* c, GemmOp op, int B, const int8_t* d_s, const float* coef, float* grad,
+                        cudaStream_t st) {
+  if (c->prec == VQMC_PREC_BF16) {
+    GemmArgs<bf16> a = make_args<bf16>(c, op, B, d_s, coef, grad);
+    if (op == kOpEloc) a.Bm = (const bf16*)c->J_hi, a.Bm2 = (const bf16*)c->J_lo;
+    if (gemm_tc_available()) return launch_gemm_tc_bf16(a, st);
+    return launch_gemm_simt_bf16(a, st);
+  }
+  GemmArgs<float> a = make_args<float>(c, op, B, d_s, coef, grad);
+  if (op == kOpEloc) a.Bm = c->J;
+  return launch_gemm_simt_f32(a, st);
+}
+
+}  // namespace vqmc
+
+namespace {
+
+// Backward of log pi w.r.t. theta with per-sample weights gout (Sec. 2.1,
+// chain rule through the MADE layer of Sec. 2.3).  Requires Sx/St to hold the
+// spins.  Recomputes H instead of keeping it from any earlier forward pass.
+vqmc_status backward_from_operands(vqmc_ctx* c, int B, const int8_t* d_s, const float* gout, float* grad,
+                                   cudaStream_t st) {
+  const int n = c->n, h = c->h;
+  const int mtiles = (B + 127) / 128;
+  VQ_CUDA(launch_gemm(c, kOpHidden, B, d_s, nullptr, nullptr, st));
+  VQ_CUDA(launch_gemm(c, kOpOut, B, d_s, gout, nullptr, st));
+  VQ_CUDA(launch_col_sum(c, n, mtiles, grad + (size_t)2 * n * h + h, st));  // db2
+  VQ_CUDA(launch_gemm(c, kOpDV, B, d_s, nullptr, grad, st));                // dW2
+  VQ_CUDA(launch_gemm(c, kOpGA, B, d_s, nullptr, nullptr, st));
+  VQ_CUDA(launch_col_sum(c, h, mtiles, grad + (size_t)n * h, st));          // db1
+  VQ_CUDA(launch_gemm(c, kOpDW, B, d_s, nullptr, grad, st));                // dW1^T
+  return VQMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vqmc_last_error(void) { return g_last_error.c_str(); }
+
+vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_ctx** out) {
+  if (!cfg || !inst || !out) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const int n = cfg->n, h = cfg->h, Bmax = cfg->max_batch;
+  if (n < 1 || h < 1 || Bmax < 1) return fail(VQMC_ERR_INVALID_ARG, "n, h and max_batch must be >= 1");
+  if (cfg->act != VQMC_ACT_RELU && cfg->act != VQMC_ACT_SIGMOID) return fail(VQMC_ERR_INVALID_ARG, "bad act");
+  if (cfg->precision != VQMC_PREC_FP32 && cfg->precision != VQMC_PREC_BF16)
+    return fail(VQMC_ERR_INVALID_ARG, "bad precision");
+  if (inst->n != n) return fail(VQMC_ERR_INVALID_ARG, "instance n differs from config n");
+  const int kind = inst->kind;
+  if (kind == VQMC_HAM_SPARSE_I32 || kind == VQMC_HAM_SPARSE_F32) {
+    if (!inst->row_ptr || inst->nnz < 0 || (inst->nnz > 0 && (!inst->col || !inst->w)))
+      return fail(VQMC_ERR_INVALID_ARG, "sparse instance needs row_ptr, col, w");
+    if (inst->row_ptr[0] != 0 || inst->row_ptr[n] != inst->nnz)
+      return fail(VQMC_ERR_INVALID_ARG, "row_ptr must start at 0 and end at nnz");
+    for (int i = 0; i < n; ++i) {
+      if (inst->row_ptr[i + 1] < inst->row_ptr[i]) return fail(VQMC_ERR_INVALID_ARG, "row_ptr not monotone");
+      for (int p = inst->row_ptr[i]; p < inst->row_ptr[i + 1]; ++p)
+        if (inst->col[p] <= i || inst->col[p] >= n)
+          return fail(VQMC_ERR_INVALID_ARG, "col must hold the strict upper triangle (i < j < n)");
+    }
+    if ((size_t)n * 4 > 200 * 1024) return fail(VQMC_ERR_UNSUPPORTED, "sparse energy supports n <= 51200");
+  } else if (kind == VQMC_HAM_DENSE_F32) {
+    if (!inst->J) return fail(VQMC_ERR_INVALID_ARG, "dense instance needs J");
+  } else {
+    return fail(VQMC_ERR_INVALID_ARG, "bad instance kind");
+  }
+  if (pad_up(h) > 2048) return fail(VQMC_ERR_UNSUPPORTED, "this build samples with h <= 2048");
+
+  vqmc_ctx* c = new vqmc_ctx();
+  c->cfg = *cfg;
+  c->n = n, c->h = h, c->Bmax = Bmax;
+  c->np = pad_up(n), c->hp = pad_up(h), c->Bp = pad_up(Bmax);
+  c->act = cfg->act, c->prec = cfg->precision, c->ham = kind;
+  c->nnz = (kind == VQMC_HAM_DENSE_F32) ? 0 : inst->nnz;
+  c->d = 2ll * n * h + h + n;
+  auto cleanup_fail = [&](vqmc_status s, const std::string& m) {
+    vqmc_destroy(c);
+    return fail(s, m);
+  };
+#define VQ_ALLOC(ptr, bytes)                                                                         \
+  do {                                                                                               \
+    cudaError_t e_ = dalloc(&(ptr), (bytes));                                                        \
+    if (e_ != cudaSuccess)                                                                           \
+      return cleanup_fail(e_ == cudaErrorMemoryAllocation ? VQMC_ERR_OOM : VQMC_ERR_CUDA,             \
+                          std::string("allocation of " #ptr ": ") + cudaGetErrorString(e_));        \
+  } while (0)
+  if (cudaGetDevice(&c->device) != cudaSuccess) return cleanup_fail(VQMC_ERR_CUDA, "no CUDA device");
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+
+  const size_t es = esize(c);
+  VQ_ALLOC(c->theta, c->d * 4);
+  VQ_ALLOC(c->adam_m, c->d * 4);
+  VQ_ALLOC(c->adam_v, c->d * 4);
+  VQ_ALLOC(c->grad, c->d * 4);
+  c->b1 = c->theta + (size_t)n * h;
+  c->b2 = c->theta + (size_t)2 * n * h + h;
+  VQ_ALLOC(c->wt_s, (size_t)n * c->hp * es);
+  VQ_ALLOC(c->v_s, (size_t)n * c->hp * es);
+  VQ_ALLOC(c->w_s, (size_t)h * c->np * es);
+  VQ_ALLOC(c->vt_s, (size_t)h * c->np * es);
+
+  VQ_ALLOC(c->S, (size_t)Bmax * n);
+  VQ_ALLOC(c->E, (size_t)Bmax * 4);
+  VQ_ALLOC(c->Sx, (size_t)Bmax * c->np * es);
+  VQ_ALLOC(c->St, (size_t)n * c->Bp * es);
+  VQ_ALLOC(c->H, (size_t)Bmax * c->hp * es);
+  VQ_ALLOC(c->Ht, (size_t)h * c->Bp * es);
+  VQ_ALLOC(c->D, (size_t)Bmax * c->np * es);
+  VQ_ALLOC(c->Dt, (size_t)n * c->Bp * es);
+  VQ_ALLOC(c->GAt, (size_t)h * c->Bp * es);
+  VQ_ALLOC(c->logp, (size_t)Bmax * 4);
+  VQ_ALLOC(c->coef, (size_t)Bmax * 4);
+  VQ_ALLOC(c->stats, 8 * sizeof(double));
+  c->row_part_tiles = (n + 127) / 128;
+  c->row_part_ld = c->Bp;
+  VQ_ALLOC(c->row_part, (size_t)c->row_part_tiles * c->row_part_ld * 4);
+  c->col_part_tiles = (Bmax + 127) / 128;
+  c->col_part_ld = c->np > c->hp ? c->np : c->hp;
+  VQ_ALLOC(c->col_part, (size_t)c->col_part_tiles * c->col_part_ld * 4);
+  VQ_ALLOC(c->err, 16);
+  VQ_ALLOC(c->step_stats, sizeof(vqmc_step_stats));
+
+  // instance
+  uint64_t hsh = 1469598103934665603ull;
+  hsh = fnv1a(hsh, &kind, sizeof(kind));
+  if (kind == VQMC_HAM_DENSE_F32) {
+    std::vector<float> Jp((size_t)n * c->np, 0.0f);
+    for (int i = 0; i < n; ++i) std::memcpy(&Jp[(size_t)i * c->np], inst->J + (size_t)i * n, (size_t)n * 4);
+    hsh = fnv1a(hsh, inst->J, (size_t)n * n * 4);
+    VQ_ALLOC(c->J, Jp.size() * 4);
+    if (cudaMemcpy(c->J, Jp.data(), Jp.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup_fail(VQMC_ERR_CUDA, "copy of J failed");
+    if (c->prec == VQMC_PREC_BF16) {
+      VQ_ALLOC(c->J_hi, Jp.size() * 2);
+      VQ_ALLOC(c->J_lo, Jp.size() * 2);
+      if (launch_dense_split(c, 0) != cudaSuccess) return cleanup_fail(VQMC_ERR_CUDA, "split of J failed");
+    }
+  } else {
+    VQ_ALLOC(c->row_ptr, (size_t)(n + 1) * 4);
+    VQ_ALLOC(c->col, (size_t)c->nnz * 4);
+    VQ_ALLOC(c->w, (size_t)c->nnz * 4);
+    bool ok = cudaMemcpy(c->row_ptr, inst->row_ptr, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (c->nnz > 0) {
+      ok = ok && cudaMemcpy(c->col, inst->col, (size_t)c->nnz * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+      ok = ok && cudaMemcpy(c->w, inst->w, (size_t)c->nnz * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    hsh = fnv1a(hsh, inst->row_ptr, (size_t)(n + 1) * 4);
+    hsh = fnv1a(hsh, inst->col, (size_t)c->nnz * 4);
+    hsh = fnv1a(hsh, inst->w, (size_t)c->nnz * 4);
+    if (!ok) return cleanup_fail(VQMC_ERR_CUDA, "copy of the instance failed");
+  }
+  if (inst->field) {
+    VQ_ALLOC(c->field, (size_t)n * 4);
+    if (cudaMemcpy(c->field, inst->field, (size_t)n * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup_fail(VQMC_ERR_CUDA, "copy of the field failed");
+    hsh = fnv1a(hsh, inst->field, (size_t)n * 4);
+  }
+  c->cfg.reserved = 0;
+  c->inst_hash = hsh;
+  if (launch_refresh_weights(c, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+    return cleanup_fail(VQMC_ERR_CUDA, "initial weight refresh failed");
+#undef VQ_ALLOC
+  *out = c;
+  return VQMC_OK;
+}
+
+void vqmc_destroy(vqmc_ctx* c) {
+  if (!c) return;
+  if (c->events) {
+    for (int64_t q = 0; q < kMaxTimedSteps * (VQMC_NUM_PARTS + 1); ++q) cudaEventDestroy(c->events[q]);
+    delete[] c->events;
+  }
+  void* ptrs[] = {c->theta, c->adam_m, c->adam_v, c->grad, c->wt_s, c->v_s, c->w_s, c->vt_s, c->row_ptr,
+                  c->col, c->w, c->field, c->J, c->J_hi, c->J_lo, c->S, c->E, c->Sx, c->St, c->H, c->Ht,
+                  c->D, c->Dt, c->GAt, c->logp, c->coef, c->stats, c->row_part, c->col_part, c->err,
+                  c->step_stats};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+int64_t vqmc_num_params(const vqmc_ctx* c) { return c ? c->d : 0; }
+
+float* vqmc_params_device(vqmc_ctx* c) { return c ? c->theta : nullptr; }
+
+uint64_t vqmc_iteration(const vqmc_ctx* c) { return c ? c->iter : 0; }
+
+vqmc_status vqmc_params_updated(vqmc_ctx* c, vqmc_stream stream) {
+  if (!c) return fail(VQMC_ERR_INVALID_ARG, "null context");
+  VQ_CUDA(launch_mask_params(c, S(stream)));
+  VQ_CUDA(launch_refresh_weights(c, S(stream)));
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_set_params(vqmc_ctx* c, const float* theta, int on_device, vqmc_stream stream) {
+  if (!c || !theta) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  VQ_CUDA(cudaMemcpyAsync(c->theta, theta, c->d * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          S(stream)));
+  VQ_CUDA(cudaMemsetAsync(c->adam_m, 0, c->d * 4, S(stream)));
+  VQ_CUDA(cudaMemsetAsync(c->adam_v, 0, c->d * 4, S(stream)));
+  c->adam_t = 0;
+  vqmc_status s = vqmc_params_updated(c, stream);
+  if (s != VQMC_OK) return s;
+  if (!on_device) VQ_CUDA(cudaStreamSynchronize(S(stream)));
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_get_params(vqmc_ctx* c, float* theta, int on_device, vqmc_stream stream) {
+  if (!c || !theta) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  VQ_CUDA(cudaMemcpyAsync(theta, c->theta, c->d * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          S(stream)));
+  if (!on_device) VQ_CUDA(cudaStreamSynchronize(S(stream)));
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_uniforms(vqmc_ctx* c, int32_t B, uint64_t iteration, float* d_u, vqmc_stream stream) {
+  vqmc_status s = check_B(c, B);
+  if (s != VQMC_OK) return s;
+  if (B > 0 && !d_u) return fail(VQMC_ERR_INVALID_ARG, "null output");
+  VQ_CUDA(launch_uniforms(B, c->n, c->cfg.seed, iteration, d_u, S(stream)));
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_sample(vqmc_ctx* c, int32_t B, const float* d_u, uint64_t iteration, int8_t* d_s, float* d_logp,
+                        vqmc_stream stream) {
+  vqmc_status s = check_B(c, B);
+  if (s != VQMC_OK) return s;
+  if (B > 0 && !d_s) return fail(VQMC_ERR_INVALID_ARG, "null output");
+  VQ_CUDA(launch_sampler(c, B, d_u, iteration, d_s, d_logp, nullptr, nullptr, S(stream)));
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_local_energy(vqmc_ctx* c, int32_t B, const int8_t* d_s, void* d_e, vqmc_stream stream) {
+  vqmc_status s = check_B(c, B);
+  if (s != VQMC_OK) return s;
+  if (B == 0) return VQMC_OK;
+  if (!d_s || !d_e) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  if (c->ham == VQMC_HAM_DENSE_F32) {
+    VQ_CUDA(launch_spins_to_operands(c, B, d_s, c->Sx, nullptr, S(stream)));
+    VQ_CUDA(launch_gemm(c, kOpEloc, B, d_s, nullptr, nullptr, S(stream)));
+    VQ_CUDA(launch_eloc_dense_finish(c, B, d_s, d_e, S(stream)));
+  } else {
+    VQ_CUDA(launch_eloc_sparse(c, B, d_s, d_e, S(stream)));
+  }
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_logprob(vqmc_ctx* c, int32_t B, const int8_t* d_s, float* d_logp, vqmc_stream stream) {
+  vqmc_status s = check_B(c, B);
+  if (s != VQMC_OK) return s;
+  if (B == 0) return VQMC_OK;
+  if (!d_s || !d_logp) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  VQ_CUDA(launch_spins_to_operands(c, B, d_s, c->Sx, nullptr, S(stream)));
+  VQ_CUDA(launch_gemm(c, kOpHidden, B, d_s, nullptr, nullptr, S(stream)));
+  VQ_CUDA(launch_gemm(c, kOpOut, B, d_s, nullptr, nullptr, S(stream)));
+  VQ_CUDA(launch_row_sum(c, B, c->row_part_tiles, d_logp, S(stream)));
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_logprob_backward(vqmc_ctx* c, int32_t B, const int8_t* d_s, const float* d_gout, float* d_grad,
+                                  vqmc_stream stream) {
+  vqmc_status s = check_B(c, B);
+  if (s != VQMC_OK) return s;
+  if (!d_grad) return fail(VQMC_ERR_INVALID_ARG, "null gradient");
+  if (B == 0) {
+    VQ_CUDA(cudaMemsetAsync(d_grad, 0, c->d * 4, S(stream)));
+    return VQMC_OK;
+  }
+  if (!d_s || !d_gout) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  VQ_CUDA(launch_spins_to_operands(c, B, d_s, c->Sx, c->St, S(stream)));
+  return backward_from_operands(c, B, d_s, d_gout, d_grad, S(stream));
+}
+
+vqmc_status vqmc_energy_stats(vqmc_ctx* c, int32_t B, const void* d_e, double* d_stats, float* d_coef,
+                              vqmc_stream stream) {
+  vqmc_status s = check_B(c, B);
+  if (s != VQMC_OK) return s;
+  if (B == 0) return VQMC_OK;
+  if (!d_e || !d_stats) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  VQ_CUDA(launch_stats(c, B, d_e, d_stats, d_coef, S(stream)));
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_grad(vqmc_ctx* c, int32_t B, const int8_t* d_s, const void* d_e, float* d_grad, double* d_stats,
+                      vqmc_stream stream) {
+  vqmc_status s = check_B(c, B);
+  if (s != VQMC_OK) return s;
+  if (!d_grad) return fail(VQMC_ERR_INVALID_ARG, "null gradient");
+  if (B == 0) {
+    VQ_CUDA(cudaMemsetAsync(d_grad, 0, c->d * 4, S(stream)));
+    return VQMC_OK;
+  }
+  if (!d_s || !d_e) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  VQ_CUDA(launch_stats(c, B, d_e, d_stats ? d_stats : c->stats, c->coef, S(stream)));
+  VQ_CUDA(launch_spins_to_operands(c, B, d_s, c->Sx, c->St, S(stream)));
+  return backward_from_operands(c, B, d_s, c->coef, d_grad, S(stream));
+}
+
+vqmc_status vqmc_adam(vqmc_ctx* c, const float* d_grad, vqmc_stream stream) {
+  if (!c || !d_grad) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  VQ_CUDA(launch_adam(c, d_grad, S(stream)));
+  return VQMC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+__global__ void fill_step_stats(const double* st, uint64_t it, const uint32_t* err, vqmc_step_stats* out) {
+  out->mean = st[0];
+  out->var = st[1];
+  out->min = st[2];
+  out->max = st[3];
+  out->iteration = it;
+  out->error_flags = *err;
+  out->reserved = 0;
+}
+}  // namespace
+
+extern "C" {
+
+vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stats* h_out) {
+  vqmc_status s = check_B(c, B);
+  if (s != VQMC_OK) return s;
+  if (B == 0) return fail(VQMC_ERR_INVALID_ARG, "vqmc_step needs B >= 1");
+  cudaStream_t st = S(stream);
+  const bool timed = c->timing && c->timed_steps < kMaxTimedSteps;
+  cudaEvent_t* ev = timed ? c->events + c->timed_steps * (VQMC_NUM_PARTS + 1) : nullptr;
+  auto mark = [&](int part) {
+    if (ev) cudaEventRecord(ev[part], st);
+  };
+  mark(0);
+  // (a) exact samples; the sampler also writes the GEMM operand layouts
+  VQ_CUDA(launch_sampler(c, B, nullptr, c->iter, c->S, nullptr, c->Sx, c->St, st));
+  mark(1);
+  // (c) local energies
+  if (c->ham == VQMC_HAM_DENSE_F32) {
+    VQ_CUDA(launch_gemm(c, kOpEloc, B, c->S, nullptr, nullptr, st));
+    VQ_CUDA(launch_eloc_dense_finish(c, B, c->S, c->E, st));
+  } else {
+    VQ_CUDA(launch_eloc_sparse(c, B, c->S, c->E, st));
+  }
+  mark(2);
+  // (d) FP64 statistics and score-function coefficients
+  VQ_CUDA(launch_stats(c, B, c->E, c->stats, c->coef, st));
+  mark(3);
+  // (b) + adjoint: gradient with recomputed hidden activations
+  s = backward_from_operands(c, B, c->S, c->coef, c->grad, st);
+  if (s != VQMC_OK) return s;
+  mark(4);
+  VQ_CUDA(launch_adam(c, c->grad, st));
+  mark(5);
+  fill_step_stats<<<1, 1, 0, st>>>(c->stats, c->iter, c->err, c->step_stats);
+  VQ_CUDA(cudaGetLastError());
+  if (h_out) VQ_CUDA(cudaMemcpyAsync(h_out, c->step_stats, sizeof(vqmc_step_stats), cudaMemcpyDeviceToHost, st));
+  if (timed) {
+    c->timed_steps += 1;
+    // sampler, energy (2 for dense), stats, 7 gradient kernels, Adam + 3 refresh kernels, stats copy
+    c->launches += 1 + (c->ham == VQMC_HAM_DENSE_F32 ? 2 : 1) + 1 + 7 + 4 + 1;
+  }
+  c->iter += 1;
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_timing_enable(vqmc_ctx* c, int enable) {
+  if (!c) return fail(VQMC_ERR_INVALID_ARG, "null context");
+  if (enable && !c->events) {
+    c->events = new cudaEvent_t[(size_t)kMaxTimedSteps * (VQMC_NUM_PARTS + 1)];
+    for (int64_t q = 0; q < kMaxTimedSteps * (VQMC_NUM_PARTS + 1); ++q) VQ_CUDA(cudaEventCreate(&c->events[q]));
+  }
+  c->timing = enable != 0;
+  c->timed_steps = 0;
+  c->launches = 0;
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_timing_read(vqmc_ctx* c, double* ms_out, int64_t* steps_out, int64_t* launches_out) {
+  if (!c) return fail(VQMC_ERR_INVALID_ARG, "null context");
+  double acc[VQMC_NUM_PARTS] = {0};
+  for (int64_t t = 0; t < c->timed_steps; ++t) {
+    cudaEvent_t* ev = c->events + t * (VQMC_NUM_PARTS + 1);
+    VQ_CUDA(cudaEventSynchronize(ev[VQMC_NUM_PARTS]));
+    for (int p = 0; p < VQMC_NUM_PARTS; ++p) {
+      float ms = 0.0f;
+      VQ_CUDA(cudaEventElapsedTime(&ms, ev[p], ev[p + 1]));
+      acc[p] += ms;
+    }
+  }
+  if (ms_out)
+    for (int p = 0; p < VQMC_NUM_PARTS; ++p) ms_out[p] = acc[p];
+  if (steps_out) *steps_out = c->timed_steps;
+  if (launches_out) *launches_out = c->launches;
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_last_batch(vqmc_ctx* c, const int8_t** d_s, const void** d_e) {
+  if (!c) return fail(VQMC_ERR_INVALID_ARG, "null context");
+  if (d_s) *d_s = c->S;
+  if (d_e) *d_e = c->E;
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_check(vqmc_ctx* c, uint32_t* flags_out) {
+  if (!c) return fail(VQMC_ERR_INVALID_ARG, "null context");
+  VQ_CUDA(cudaDeviceSynchronize());
+  uint32_t f = 0;
+  VQ_CUDA(cudaMemcpy(&f, c->err, 4, cudaMemcpyDeviceToHost));
+  VQ_CUDA(cudaMemset(c->err, 0, 4));
+  if (flags_out) *flags_out = f;
+  if (f & VQMC_DEVERR_TIMEOUT) return fail(VQMC_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (f & VQMC_DEVERR_NONFINITE) return fail(VQMC_ERR_NONFINITE, "non-finite energy statistics");
+  return VQMC_OK;
+}
+
+// Checkpoint file: header, then theta, Adam m, Adam v (d floats each).
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t n, h, act;
+  int64_t d;
+  int64_t adam_t;
+  uint64_t iter;
+  uint64_t seed;
+  uint64_t inst_hash;
+};
+
+vqmc_status vqmc_save(vqmc_ctx* c, const char* path) {
+  if (!c || !path) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  VQ_CUDA(cudaDeviceSynchronize());
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, "VQMCCKP1", 8);
+  hd.version = 1;
+  hd.n = c->n, hd.h = c->h, hd.act = c->act, hd.d = c->d;
+  hd.adam_t = c->adam_t, hd.iter = c->iter, hd.seed = c->cfg.seed, hd.inst_hash = c->inst_hash;
+  std::vector<float> buf((size_t)c->d);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(VQMC_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+  float* arrs[3] = {c->theta, c->adam_m, c->adam_v};
+  for (float* a : arrs) {
+    if (!ok) break;
+    if (cudaMemcpy(buf.data(), a, c->d * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      std::fclose(f);
+      return fail(VQMC_ERR_CUDA, "checkpoint copy failed");
+    }
+    ok = std::fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(VQMC_ERR_INVALID_ARG, "checkpoint write failed");
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_load(vqmc_ctx* c, const char* path) {
+  if (!c || !path) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(VQMC_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  CkptHeader hd;
+  if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "VQMCCKP1", 8) != 0 || hd.version != 1) {
+    std::fclose(f);
+    return fail(VQMC_ERR_INVALID_ARG, "not a vqmc checkpoint");
+  }
+  if (hd.n != c->n || hd.h != c->h || hd.act != c->act || hd.d != c->d || hd.inst_hash != c->inst_hash) {
+    std::fclose(f);
+    return fail(VQMC_ERR_INVALID_ARG, "checkpoint does not match this context (shape, activation or instance)");
+  }
+  std::vector<float> buf((size_t)c->d);
+  float* arrs[3] = {c->theta, c->adam_m, c->adam_v};
+  for (float* a : arrs) {
+    if (std::fread(buf.data(), 4, buf.size(), f) != buf.size()) {
+      std::fclose(f);
+      return fail(VQMC_ERR_INVALID_ARG, "truncated checkpoint");
+    }
+    if (cudaMemcpy(a, buf.data(), c->d * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      std::fclose(f);
+      return fail(VQMC_ERR_CUDA, "checkpoint copy failed");
+    }
+  }
+  std::fclose(f);
+  c->adam_t = hd.adam_t;
+  c->iter = hd.iter;
+  c->cfg.seed = hd.seed;
+  VQ_CUDA(launch_refresh_weights(c, 0));
+  VQ_CUDA(cudaDeviceSynchronize());
+  return VQMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,398 @@
+"""Python binding of libvqmc (include/vqmc.h): argument marshalling only.
+
+Every compute step runs in the CUDA library; this module converts torch
+tensors to raw pointers and the current torch stream to a cudaStream_t.  The
+functions carry the C names (``vqmc_create``, ``vqmc_sample``, ...); ``VQMC``
+is a small convenience class over them and ``LogProb`` is the
+``torch.autograd.Function`` whose backward is the library's hand-written
+adjoint (``vqmc_logprob_backward``).
+
+There is no CPU fallback: importing the library fails loudly when
+``lib/libvqmc.so`` has not been built (``paper_2106_13308_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libvqmc.so")
+
+VQMC_OK, VQMC_ERR_INVALID_ARG, VQMC_ERR_CUDA, VQMC_ERR_OOM = 0, 1, 2, 3
+VQMC_ERR_NONFINITE, VQMC_ERR_TIMEOUT, VQMC_ERR_UNSUPPORTED = 4, 5, 6
+ACT = {"relu": 0, "sigmoid": 1}
+PREC = {"fp32": 0, "bf16": 1}
+HAM = {"sparse_i32": 0, "sparse_f32": 1, "dense": 2}
+DEVERR_TIMEOUT, DEVERR_NONFINITE = 1, 2
+
+# Names declared in include/vqmc.h (the CPU test checks the library exports them).
+EXPORTS = [
+    "vqmc_create", "vqmc_destroy", "vqmc_num_params", "vqmc_set_params", "vqmc_get_params",
+    "vqmc_params_device", "vqmc_params_updated", "vqmc_uniforms", "vqmc_sample", "vqmc_local_energy",
+    "vqmc_logprob", "vqmc_logprob_backward", "vqmc_energy_stats", "vqmc_grad", "vqmc_adam", "vqmc_step",
+    "vqmc_last_batch", "vqmc_iteration", "vqmc_check", "vqmc_save", "vqmc_load", "vqmc_timing_enable",
+    "vqmc_timing_read", "vqmc_last_error",
+]
+PARTS = ["sample", "energy", "stats", "grad", "adam"]
+
+
+class VQMCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"vqmc status {status}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("h", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("act", ctypes.c_int32), ("precision", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("reserved", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("nnz", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("w", ctypes.c_void_p), ("field", ctypes.c_void_p), ("J", ctypes.c_void_p)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_double), ("var", ctypes.c_double), ("min", ctypes.c_double),
+                ("max", ctypes.c_double), ("iteration", ctypes.c_uint64), ("error_flags", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libvqmc.so and declares the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2106_13308_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    st = ctypes.c_int
+    sig = {
+        "vqmc_create": (st, [ctypes.POINTER(Config), ctypes.POINTER(Instance), ctypes.POINTER(P)]),
+        "vqmc_destroy": (None, [P]),
+        "vqmc_num_params": (I64, [P]),
+        "vqmc_set_params": (st, [P, P, ctypes.c_int, P]),
+        "vqmc_get_params": (st, [P, P, ctypes.c_int, P]),
+        "vqmc_params_device": (P, [P]),
+        "vqmc_params_updated": (st, [P, P]),
+        "vqmc_uniforms": (st, [P, I32, U64, P, P]),
+        "vqmc_sample": (st, [P, I32, P, U64, P, P, P]),
+        "vqmc_local_energy": (st, [P, I32, P, P, P]),
+        "vqmc_logprob": (st, [P, I32, P, P, P]),
+        "vqmc_logprob_backward": (st, [P, I32, P, P, P, P]),
+        "vqmc_energy_stats": (st, [P, I32, P, P, P, P]),
+        "vqmc_grad": (st, [P, I32, P, P, P, P, P]),
+        "vqmc_adam": (st, [P, P, P]),
+        "vqmc_step": (st, [P, I32, P, ctypes.POINTER(StepStats)]),
+        "vqmc_last_batch": (st, [P, ctypes.POINTER(P), ctypes.POINTER(P)]),
+        "vqmc_iteration": (U64, [P]),
+        "vqmc_check": (st, [P, ctypes.POINTER(ctypes.c_uint32)]),
+        "vqmc_save": (st, [P, ctypes.c_char_p]),
+        "vqmc_load": (st, [P, ctypes.c_char_p]),
+        "vqmc_timing_enable": (st, [P, ctypes.c_int]),
+        "vqmc_timing_read": (st, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "vqmc_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != VQMC_OK:
+        raise VQMCError(status, _lib.vqmc_last_error().decode())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- C names
+
+def vqmc_create(cfg: Config, inst: Instance) -> ctypes.c_void_p:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.vqmc_create(ctypes.byref(cfg), ctypes.byref(inst), ctypes.byref(h)))
+    return h
+
+
+def vqmc_destroy(ctx):
+    load_library().vqmc_destroy(ctx)
+
+
+def vqmc_num_params(ctx) -> int:
+    return int(load_library().vqmc_num_params(ctx))
+
+
+def vqmc_set_params(ctx, theta: torch.Tensor, stream=None):
+    if theta.is_cuda:
+        _check(load_library().vqmc_set_params(ctx, _ptr(theta), 1, _stream(stream)))
+    else:
+        t = np.ascontiguousarray(theta.detach().numpy() if isinstance(theta, torch.Tensor) else theta,
+                                 dtype=np.float32)
+        _check(load_library().vqmc_set_params(ctx, t.ctypes.data_as(ctypes.c_void_p), 0, _stream(stream)))
+
+
+def vqmc_get_params(ctx, out: torch.Tensor, stream=None):
+    if out.is_cuda:
+        _check(load_library().vqmc_get_params(ctx, _ptr(out), 1, _stream(stream)))
+    else:
+        assert out.dtype == torch.float32 and out.is_contiguous()
+        _check(load_library().vqmc_get_params(ctx, ctypes.c_void_p(out.data_ptr()), 0, _stream(stream)))
+
+
+def vqmc_params_updated(ctx, stream=None):
+    _check(load_library().vqmc_params_updated(ctx, _stream(stream)))
+
+
+def vqmc_uniforms(ctx, B: int, iteration: int, u: torch.Tensor, stream=None):
+    _check(load_library().vqmc_uniforms(ctx, B, iteration, _ptr(u), _stream(stream)))
+
+
+def vqmc_sample(ctx, B: int, u, iteration: int, s: torch.Tensor, logp=None, stream=None):
+    _check(load_library().vqmc_sample(ctx, B, _ptr(u), iteration, _ptr(s), _ptr(logp), _stream(stream)))
+
+
+def vqmc_local_energy(ctx, B: int, s: torch.Tensor, e: torch.Tensor, stream=None):
+    _check(load_library().vqmc_local_energy(ctx, B, _ptr(s), _ptr(e), _stream(stream)))
+
+
+def vqmc_logprob(ctx, B: int, s: torch.Tensor, logp: torch.Tensor, stream=None):
+    _check(load_library().vqmc_logprob(ctx, B, _ptr(s), _ptr(logp), _stream(stream)))
+
+
+def vqmc_logprob_backward(ctx, B: int, s, gout, grad, stream=None):
+    _check(load_library().vqmc_logprob_backward(ctx, B, _ptr(s), _ptr(gout), _ptr(grad), _stream(stream)))
+
+
+def vqmc_energy_stats(ctx, B: int, e, stats, coef=None, stream=None):
+    _check(load_library().vqmc_energy_stats(ctx, B, _ptr(e), _ptr(stats), _ptr(coef), _stream(stream)))
+
+
+def vqmc_grad(ctx, B: int, s, e, grad, stats=None, stream=None):
+    _check(load_library().vqmc_grad(ctx, B, _ptr(s), _ptr(e), _ptr(grad), _ptr(stats), _stream(stream)))
+
+
+def vqmc_adam(ctx, grad, stream=None):
+    _check(load_library().vqmc_adam(ctx, _ptr(grad), _stream(stream)))
+
+
+def vqmc_step(ctx, B: int, out: StepStats | None = None, stream=None):
+    _check(load_library().vqmc_step(ctx, B, _stream(stream), ctypes.byref(out) if out is not None else None))
+
+
+def vqmc_check(ctx) -> int:
+    f = ctypes.c_uint32()
+    st = load_library().vqmc_check(ctx, ctypes.byref(f))
+    if st not in (VQMC_OK, VQMC_ERR_TIMEOUT, VQMC_ERR_NONFINITE):
+        _check(st)
+    return int(f.value)
+
+
+def vqmc_timing_enable(ctx, enable: bool):
+    _check(load_library().vqmc_timing_enable(ctx, 1 if enable else 0))
+
+
+def vqmc_timing_read(ctx):
+    """({part: ms summed over recorded steps}, steps, kernel launches)."""
+    ms = (ctypes.c_double * len(PARTS))()
+    steps, launches = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().vqmc_timing_read(ctx, ms, ctypes.byref(steps), ctypes.byref(launches)))
+    return dict(zip(PARTS, list(ms))), int(steps.value), int(launches.value)
+
+
+def vqmc_save(ctx, path: str):
+    _check(load_library().vqmc_save(ctx, path.encode()))
+
+
+def vqmc_load(ctx, path: str):
+    _check(load_library().vqmc_load(ctx, path.encode()))
+
+
+# --------------------------------------------------------------- wrapper
+
+class _DeviceArray:
+    """Exposes a raw device pointer through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, n: int, typestr: str = "<f4"):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class VQMC:
+    """One GPU context: model, instance, optimiser and workspaces.
+
+    ``instance`` is a dict as produced by ``paper_2106_13308_gb300.inputs``
+    (kind sparse_i32 / sparse_f32 with row_ptr, col, w[, field]; or dense with
+    J)."""
+
+    def __init__(self, n, h, max_batch, instance, act="relu", precision="bf16", lr=1e-2, beta1=0.9,
+                 beta2=0.999, eps=1e-8, seed=0):
+        load_library()
+        self.n, self.h, self.max_batch = int(n), int(h), int(max_batch)
+        self.act, self.precision = act, precision
+        self.kind = instance["kind"]
+        cfg = Config(self.n, self.h, self.max_batch, ACT[act], PREC[precision], lr, beta1, beta2, eps, 0,
+                     int(seed) & (2 ** 64 - 1))
+        keep = []
+
+        def arr(a, dt):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data_as(ctypes.c_void_p)
+
+        if self.kind == "dense":
+            inst = Instance(HAM["dense"], self.n, 0, 0, None, None, None,
+                            arr(instance.get("field"), np.float32), arr(instance["J"], np.float32))
+        else:
+            wdt = np.int32 if self.kind == "sparse_i32" else np.float32
+            inst = Instance(HAM[self.kind], self.n, int(len(instance["col"])), 0,
+                            arr(instance["row_ptr"], np.int32), arr(instance["col"], np.int32),
+                            arr(instance["w"], wdt), arr(instance.get("field"), wdt), None)
+        self.ctx = vqmc_create(cfg, inst)
+        self.d = vqmc_num_params(self.ctx)
+        self.e_dtype = torch.int32 if self.kind == "sparse_i32" else torch.float32
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            vqmc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # parameters
+    def set_params(self, theta):
+        vqmc_set_params(self.ctx, torch.as_tensor(theta))
+
+    def get_params(self) -> torch.Tensor:
+        out = torch.empty(self.d, dtype=torch.float32)
+        vqmc_get_params(self.ctx, out)
+        return out
+
+    def params_view(self) -> torch.Tensor:
+        """Zero-copy CUDA view of the master theta (valid while the context lives)."""
+        ptr = load_library().vqmc_params_device(self.ctx)
+        return torch.as_tensor(_DeviceArray(ptr, self.d), device="cuda")
+
+    # the path
+    def uniforms(self, B, iteration):
+        u = torch.empty((B, self.n), dtype=torch.float32, device="cuda")
+        vqmc_uniforms(self.ctx, B, iteration, u)
+        return u
+
+    def sample(self, B, u=None, iteration=0):
+        s = torch.empty((B, self.n), dtype=torch.int8, device="cuda")
+        lp = torch.empty(B, dtype=torch.float32, device="cuda")
+        vqmc_sample(self.ctx, B, u, iteration, s, lp)
+        return s, lp
+
+    def local_energy(self, s):
+        B = s.shape[0]
+        e = torch.empty(B, dtype=self.e_dtype, device="cuda")
+        vqmc_local_energy(self.ctx, B, s, e)
+        return e
+
+    def logprob(self, s):
+        B = s.shape[0]
+        lp = torch.empty(B, dtype=torch.float32, device="cuda")
+        vqmc_logprob(self.ctx, B, s, lp)
+        return lp
+
+    def logprob_backward(self, s, gout):
+        g = torch.empty(self.d, dtype=torch.float32, device="cuda")
+        vqmc_logprob_backward(self.ctx, s.shape[0], s, gout.contiguous().float(), g)
+        return g
+
+    def energy_stats(self, e):
+        stats = torch.empty(4, dtype=torch.float64, device="cuda")
+        coef = torch.empty(e.shape[0], dtype=torch.float32, device="cuda")
+        vqmc_energy_stats(self.ctx, e.shape[0], e, stats, coef)
+        return stats, coef
+
+    def grad(self, s, e):
+        g = torch.empty(self.d, dtype=torch.float32, device="cuda")
+        stats = torch.empty(4, dtype=torch.float64, device="cuda")
+        vqmc_grad(self.ctx, s.shape[0], s, e, g, stats)
+        return g, stats
+
+    def adam(self, g):
+        vqmc_adam(self.ctx, g)
+
+    def step(self, B, out: StepStats | None = None):
+        vqmc_step(self.ctx, B, out)
+        return out
+
+    def last_batch(self, B):
+        ps, pe = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(load_library().vqmc_last_batch(self.ctx, ctypes.byref(ps), ctypes.byref(pe)))
+        s = torch.as_tensor(_DeviceArray(ps.value, B * self.n, "|i1"), device="cuda").view(B, self.n)
+        e = torch.as_tensor(_DeviceArray(pe.value, B, "<i4" if self.e_dtype == torch.int32 else "<f4"),
+                            device="cuda")
+        return s, e
+
+    @property
+    def iteration(self) -> int:
+        return int(load_library().vqmc_iteration(self.ctx))
+
+    def check(self) -> int:
+        return vqmc_check(self.ctx)
+
+    def timing_enable(self, enable=True):
+        vqmc_timing_enable(self.ctx, enable)
+
+    def timing_read(self):
+        return vqmc_timing_read(self.ctx)
+
+    def save(self, path):
+        vqmc_save(self.ctx, path)
+
+    def load(self, path):
+        vqmc_load(self.ctx, path)
+
+
+class LogProb(torch.autograd.Function):
+    """log pi_theta(s) with the library's adjoint as backward.
+
+    ``theta`` must be ``model.params_view()`` (the context's own parameters):
+    forward reads the weight copies the context keeps in sync with it, and
+    backward returns sum_b grad_out[b] * grad_theta log pi(s_b), recomputing
+    the hidden activations instead of saving them."""
+
+    @staticmethod
+    def forward(ctx, theta, spins, model: VQMC):
+        ctx.model = model
+        ctx.save_for_backward(spins)
+        return model.logprob(spins)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (spins,) = ctx.saved_tensors
+        g = ctx.model.logprob_backward(spins, grad_out)
+        return g, None, None

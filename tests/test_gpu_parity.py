@@ -1,0 +1,251 @@
+"""GPU parity: every step of the hot path through the C ABI against the FP64
+oracle, element by element, on seeded inputs.
+
+Tolerances (written here, derived in the design notes):
+  * uniforms, samples on shared uniforms, integer energies: bit-exact
+    (samples exclude near-ties |u - p_i| < 1e-6, which are counted);
+  * log pi: relative error <= 1e-5 with FP32 weights and <= 2e-2 with BF16
+    weights (the oracle then uses the same BF16-rounded weights);
+  * gradients: ||g - g_ref|| / ||g_ref|| <= 1e-4 (FP32), <= 3e-2 (BF16);
+  * FP64 statistics given identical energies: relative 1e-12.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2106_13308_gb300 import inputs
+
+from gpu_helpers import (ACT_ORACLE, build_lib, grad_blocks, logp_rel, make_model, masked, oracle_params,
+                         rel_err, rows_without_near_ties, teacher_forced, er_instance)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_lib()
+    assert torch.cuda.is_available()
+
+
+CASES = [
+    # n, h, B, act, precision, graph p
+    (20, 40, 1024, "sigmoid", "fp32", 0.5),
+    (20, 40, 1024, "sigmoid", "bf16", 0.5),
+    (300, 200, 300, "relu", "fp32", 0.02),
+    (257, 130, 77, "relu", "bf16", 0.03),
+    (129, 500, 33, "relu", "fp32", 0.05),
+    (1000, 1000, 64, "relu", "bf16", 0.003),
+]
+
+
+# ---------------------------------------------------------------- uniforms
+
+def test_uniforms_match_oracle_philox():
+    n, h, B = 37, 16, 50
+    m = make_model(n, h, B, er_instance(n, 0.2, 1), seed=0xDEADBEEF12345)
+    for it in (0, 1, 2**33 + 5):
+        u = m.uniforms(B, it).cpu().numpy()
+        assert np.array_equal(u, oracle.uniforms(B, n, 0xDEADBEEF12345, it))
+
+
+# ----------------------------------------------------------------- sampler
+
+@pytest.mark.parametrize("n,h,B,act,prec,p", CASES)
+def test_sampler_matches_oracle(n, h, B, act, prec, p):
+    inst = er_instance(n, p, 2)
+    theta = inputs.lively_params(n, h, 3)
+    m = make_model(n, h, B, inst, act=act, precision=prec, theta=theta)
+    P = oracle_params(theta, n, h, prec)
+    U = inputs.uniforms(B, n, 4)
+    S, lp = m.sample(B, torch.from_numpy(U).cuda())
+    S, lp = S.cpu().numpy(), lp.cpu().numpy()
+    assert set(np.unique(S)) <= {-1, 1}
+    # teacher-forced: each spin decided by the oracle's conditional on its own prefix
+    mism, ties = teacher_forced(P, S, U, act)
+    assert mism == 0, (mism, ties)
+    # free-running oracle on the same uniforms: identical rows (barring near-ties)
+    So, lpo = oracle.sample(P, U, ACT_ORACLE[act])
+    rows = rows_without_near_ties(P, So, U, act)
+    assert rows.sum() >= B - 2
+    assert np.array_equal(S[rows], So[rows])
+    assert logp_rel(lp[rows], lpo[rows]) <= 1e-5
+
+
+def test_sampler_internal_philox_matches_oracle():
+    n, h, B, seed = 150, 90, 200, 777
+    inst = er_instance(n, 0.05, 5)
+    theta = inputs.lively_params(n, h, 6)
+    m = make_model(n, h, B, inst, theta=theta, seed=seed)
+    P = oracle_params(theta, n, h, "fp32")
+    for it in (0, 9):
+        S, lp = m.sample(B, None, iteration=it)
+        S = S.cpu().numpy()
+        U = oracle.uniforms(B, n, seed, it)
+        So, lpo = oracle.sample(P, U)
+        rows = rows_without_near_ties(P, So, U, "relu")
+        assert rows.sum() >= B - 2
+        assert np.array_equal(S[rows], So[rows])
+
+
+def test_sampler_edge_sizes():
+    # B = 1, B = 0 (no-op), n = 1 (a single conditional sigma(c_1)), h = 1
+    for n, h, B in [(1, 1, 5), (2, 1, 17), (5, 64, 1), (64, 3, 40)]:
+        inst = er_instance(n, 0.5, 7) if n > 1 else inputs.to_csr(1, np.zeros((0, 2), np.int64), np.zeros(0, np.int32))
+        theta = inputs.lively_params(n, h, 8)
+        m = make_model(n, h, B, inst, theta=theta)
+        P = oracle_params(theta, n, h, "fp32")
+        U = inputs.uniforms(B, n, 9)
+        S, lp = m.sample(B, torch.from_numpy(U).cuda())
+        So, lpo = oracle.sample(P, U)
+        rows = rows_without_near_ties(P, So, U, "relu")
+        assert np.array_equal(S.cpu().numpy()[rows], So[rows])
+        assert logp_rel(lp.cpu().numpy()[rows], lpo[rows]) <= 1e-5
+        s0 = torch.empty((0, n), dtype=torch.int8, device="cuda")
+        from paper_2106_13308_gb300 import vqmc
+        vqmc.vqmc_sample(m.ctx, 0, None, 0, s0)
+
+
+# ----------------------------------------------------------- local energy
+
+def test_sparse_energy_bit_exact():
+    for n, p, B, seed in [(300, 0.02, 300, 11), (10000, 8 / 9999, 97, 12), (64, 0.9, 1000, 13)]:
+        inst = er_instance(n, p, seed)
+        m = make_model(n, 8, B, inst)
+        S = inputs.spins(B, n, seed + 100)
+        E = m.local_energy(torch.from_numpy(S).cuda()).cpu().numpy()
+        Eo = oracle.energy(inst, S)
+        assert E.dtype == np.int32 and np.array_equal(E.astype(np.float64), Eo)
+        # Max-Cut mapping: cut = (W_tot - E)/2
+        assert np.array_equal((inst["w"].sum() - E) // 2, oracle.cut(inst, S).astype(np.int64))
+
+
+def test_sparse_energy_with_field_and_pm1_weights():
+    n, B = 1000, 130
+    e = inputs.random_regular(n, 3, 21)
+    inst = inputs.to_csr(n, e, inputs.pm1_weights(len(e), 22), field=inputs.int_weights(n, -3, 3, 23))
+    m = make_model(n, 16, B, inst)
+    S = inputs.spins(B, n, 24)
+    E = m.local_energy(torch.from_numpy(S).cuda()).cpu().numpy()
+    assert np.array_equal(E.astype(np.float64), oracle.energy(inst, S))
+
+
+def test_sparse_float_energy():
+    n, B = 500, 64
+    e = inputs.erdos_renyi(n, 0.01, 31)
+    w = np.random.default_rng(32).standard_normal(len(e)).astype(np.float32)
+    inst = inputs.to_csr(n, e, w)
+    m = make_model(n, 16, B, inst)
+    S = inputs.spins(B, n, 33)
+    E = m.local_energy(torch.from_numpy(S).cuda()).cpu().numpy()
+    Eo = oracle.energy(inst, S)
+    # FP32 accumulation of m terms of size O(1): |err| <= m * 2^-24 * max|partial|
+    assert np.max(np.abs(E - Eo)) <= len(e) * 2.0 ** -23 * (np.abs(w).sum())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_dense_energy(prec):
+    n, B = 300, 200
+    inst = inputs.sk(n, 41)
+    m = make_model(n, 16, B, inst, precision=prec)
+    S = inputs.spins(B, n, 42)
+    E = m.local_energy(torch.from_numpy(S).cuda()).cpu().numpy()
+    Eo = oracle.energy(inst, S)
+    scale = np.sqrt(np.sum(inst["J"].astype(np.float64) ** 2))  # ~ ||J||_F
+    err = np.max(np.abs(E - Eo))
+    # FP32 products are exact for s = +-1; BF16 hi/lo keeps 16 mantissa bits of J
+    bound = (n * n * 2.0 ** -23 if prec == "fp32" else n * n * 2.0 ** -16) * np.abs(inst["J"]).max()
+    assert err <= bound, (err, bound, scale)
+
+
+# ------------------------------------------------------------- statistics
+
+def test_energy_stats_fp64():
+    n, B = 100, 777
+    inst = er_instance(n, 0.1, 51)
+    m = make_model(n, 8, B, inst)
+    S = inputs.spins(B, n, 52)
+    E = m.local_energy(torch.from_numpy(S).cuda())
+    st, coef = m.energy_stats(E)
+    sto, coefo = oracle.stats(oracle.energy(inst, S))
+    assert np.allclose(st.cpu().numpy(), sto, rtol=1e-12, atol=0)
+    assert np.allclose(coef.cpu().numpy(), coefo, rtol=1e-6, atol=1e-12)
+
+
+# ---------------------------------------------------------------- log prob
+
+@pytest.mark.parametrize("n,h,B,act,prec,p", CASES)
+def test_logprob_gemm_matches_oracle(n, h, B, act, prec, p):
+    inst = er_instance(n, p, 61)
+    theta = inputs.lively_params(n, h, 62)
+    m = make_model(n, h, B, inst, act=act, precision=prec, theta=theta)
+    P = oracle_params(theta, n, h, prec)
+    S = inputs.spins(B, n, 63)
+    lp = m.logprob(torch.from_numpy(S).cuda()).cpu().numpy()
+    lpo = oracle.logprob(P, S, ACT_ORACLE[act])
+    tol = 1e-5 if prec == "fp32" else 2e-2
+    assert logp_rel(lp, lpo) <= tol
+
+
+# ---------------------------------------------------------------- gradient
+
+@pytest.mark.parametrize("n,h,B,act,prec,p", CASES)
+def test_gradient_matches_oracle(n, h, B, act, prec, p):
+    inst = er_instance(n, p, 71)
+    theta = inputs.lively_params(n, h, 72)
+    m = make_model(n, h, B, inst, act=act, precision=prec, theta=theta)
+    P = oracle_params(theta, n, h, prec)
+    S = inputs.spins(B, n, 73)
+    St = torch.from_numpy(S).cuda()
+    E = m.local_energy(St)
+    g, st = m.grad(St, E)
+    (dW1, db1, dW2, db2), sto, Eo = oracle.vqmc_grad(P, inst, S, ACT_ORACLE[act])
+    go = oracle.made_to_theta(dW1, db1, dW2, db2)
+    g = g.cpu().numpy()
+    tol = 1e-4 if prec == "fp32" else 3e-2
+    assert rel_err(g, go) <= tol
+    for k, blk in grad_blocks(g, n, h).items():
+        ref = grad_blocks(go, n, h)[k]
+        if np.linalg.norm(ref) > 1e-8 * np.linalg.norm(go):
+            assert rel_err(blk, ref) <= 3 * tol, k
+    # outside the masks the gradient is exactly zero
+    mask_zero = masked(np.ones_like(theta), n, h) == 0
+    assert np.all(g[mask_zero] == 0)
+    assert np.allclose(st.cpu().numpy(), sto, rtol=1e-12)
+
+
+def test_logprob_backward_arbitrary_weights_and_autograd():
+    from paper_2106_13308_gb300.vqmc import LogProb
+    n, h, B = 90, 70, 45
+    inst = er_instance(n, 0.05, 81)
+    theta = inputs.lively_params(n, h, 82)
+    m = make_model(n, h, B, inst, theta=theta)
+    P = oracle_params(theta, n, h, "fp32")
+    S = inputs.spins(B, n, 83)
+    gout = np.random.default_rng(84).standard_normal(B).astype(np.float32)
+    go = oracle.made_to_theta(*oracle.logprob_grad(P, S, gout.astype(np.float64)))
+    St = torch.from_numpy(S).cuda()
+    g = m.logprob_backward(St, torch.from_numpy(gout).cuda()).cpu().numpy()
+    assert rel_err(g, go) <= 1e-4
+    th = m.params_view().requires_grad_(True)
+    lp = LogProb.apply(th, St, m)
+    assert logp_rel(lp.detach().cpu().numpy(), oracle.logprob(P, S)) <= 1e-5
+    lp.backward(torch.from_numpy(gout).cuda())
+    assert rel_err(th.grad.cpu().numpy(), go) <= 1e-4
+
+
+# -------------------------------------------------------------------- adam
+
+def test_adam_matches_oracle():
+    n, h = 40, 30
+    inst = er_instance(n, 0.2, 91)
+    theta = inputs.lively_params(n, h, 92)
+    m = make_model(n, h, 4, inst, theta=theta)
+    t0 = masked(theta, n, h).astype(np.float64)
+    mo, vo = np.zeros_like(t0), np.zeros_like(t0)
+    rng = np.random.default_rng(93)
+    for t in range(1, 4):
+        g = rng.standard_normal(t0.size).astype(np.float32) * masked(np.ones_like(theta), n, h)
+        m.adam(torch.from_numpy(g).cuda())
+        oracle.adam(t0, mo, vo, g.astype(np.float64), t)
+    assert np.allclose(m.get_params().numpy(), t0, rtol=0, atol=2e-6)

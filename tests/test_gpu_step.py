@@ -1,0 +1,171 @@
+"""GPU tests of the full VQMC iteration (vqmc_step) through the C ABI:
+agreement with the oracle's iteration, determinism, checkpoint/resume, the
+device error word, and the full-size workload checked on sampled outputs."""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2106_13308_gb300 import inputs
+from paper_2106_13308_gb300.vqmc import StepStats
+
+from gpu_helpers import (ACT_ORACLE, build_lib, logp_rel, make_model, masked, oracle_params, rel_err,
+                         rows_without_near_ties, teacher_forced, er_instance)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_lib()
+
+
+@pytest.mark.parametrize("act", ["relu", "sigmoid"])
+def test_step_matches_oracle_iteration(act):
+    """One vqmc_step (internal Philox) equals the oracle's iteration: same
+    samples, same energies, same FP64 statistics, and the Adam update of the
+    same score-function gradient."""
+    n, h, B, seed = 120, 96, 256, 4243
+    inst = er_instance(n, 0.05, 101)
+    theta = inputs.lively_params(n, h, 102)
+    m = make_model(n, h, B, inst, act=act, theta=theta, seed=seed, lr=1e-3)
+    out = StepStats()
+    m.step(B, out)
+    torch.cuda.synchronize()
+    S, E = m.last_batch(B)
+    S, E = S.cpu().numpy(), E.cpu().numpy()
+    P = oracle_params(theta, n, h, "fp32")
+    U = oracle.uniforms(B, n, seed, 0)
+    So, _ = oracle.sample(P, U, ACT_ORACLE[act])
+    rows = rows_without_near_ties(P, So, U, act)
+    assert rows.all(), "choose a seed without near-ties"
+    assert np.array_equal(S, So)
+    Eo = oracle.energy(inst, So)
+    assert np.array_equal(E.astype(np.float64), Eo)
+    (dW1, db1, dW2, db2), sto, _ = oracle.vqmc_grad(P, inst, So, ACT_ORACLE[act])
+    assert np.allclose([out.mean, out.var, out.min, out.max], sto, rtol=1e-12)
+    assert out.iteration == 0 and out.error_flags == 0 and m.iteration == 1
+    g = oracle.made_to_theta(dW1, db1, dW2, db2)
+    t = masked(theta, n, h).astype(np.float64)
+    oracle.adam(t, np.zeros_like(t), np.zeros_like(t), g, 1, lr=1e-3)
+    got = m.get_params().numpy().astype(np.float64)
+    # Adam's first step moves each entry by lr * g/(|g| + eps): compare where
+    # |g| is well above the FP32 noise of the gradient; elsewhere the move is
+    # bounded by lr.
+    big = np.abs(g) > 1e-4 * np.abs(g).max()
+    assert np.allclose(got[big], t[big], rtol=0, atol=1e-6)
+    assert np.all(np.abs(got - masked(theta, n, h)) <= 1e-3 + 1e-6)
+
+
+def test_steps_are_deterministic_and_checkpoint_resumes_bit_exact():
+    n, h, B = 200, 128, 128
+    inst = er_instance(n, 0.03, 111)
+    theta = inputs.made_params(n, h, 112, w_std=0.05)
+    a = make_model(n, h, B, inst, theta=theta, seed=5, precision="bf16")
+    b = make_model(n, h, B, inst, theta=theta, seed=5, precision="bf16")
+    for _ in range(3):
+        a.step(B)
+        b.step(B)
+    assert torch.equal(a.get_params(), b.get_params())
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        a.save(path)
+        for _ in range(2):
+            a.step(B)
+        c = make_model(n, h, B, inst, seed=999, precision="bf16")
+        c.load(path)
+        assert c.iteration == 3
+        for _ in range(2):
+            c.step(B)
+        assert torch.equal(a.get_params(), c.get_params())
+        # a checkpoint of another instance is refused
+        other = make_model(n, h, B, er_instance(n, 0.03, 113), precision="bf16")
+        with pytest.raises(Exception):
+            other.load(path)
+
+
+def test_training_lowers_energy_c1():
+    """Max-Cut on G(20, 0.5), MADE with 40 sigmoid units, B = 1024, 50 Adam
+    iterations at lr 1e-2: the mean energy drops and the best sample's cut
+    never exceeds the brute-force optimum."""
+    cfg = inputs.config("maxcut_er20")
+    inst = inputs.make_instance(cfg)
+    n, h, B = cfg["n"], cfg["h"], cfg["B"]
+    theta = inputs.made_params(n, h, cfg["param_seed"], w_std=cfg["w_std"])
+    for prec in ("fp32", "bf16"):
+        m = make_model(n, h, B, inst, act="sigmoid", precision=prec, theta=theta, seed=1)
+        first = last = None
+        out = StepStats()
+        for it in range(50):
+            m.step(B, out)
+            torch.cuda.synchronize()
+            if it == 0:
+                first = out.mean
+            last = out.mean
+        assert last < first - 1.0
+        best_cut = (inst["w"].sum() - out.min) / 2
+        assert best_cut <= oracle.maxcut_bruteforce(inst)
+        assert m.check() == 0
+
+
+def test_nonfinite_energy_sets_error_word():
+    """Host-side fault injection: a NaN coupling makes the energies NaN; the
+    FP64 statistics kernel flags it and vqmc_check reports it."""
+    n, B = 50, 32
+    e = inputs.erdos_renyi(n, 0.2, 121)
+    w = np.ones(len(e), dtype=np.float32)
+    w[3] = np.nan
+    inst = inputs.to_csr(n, e, w)
+    m = make_model(n, 8, B, inst)
+    S = torch.from_numpy(inputs.spins(B, n, 122)).cuda()
+    E = m.local_energy(S)
+    m.energy_stats(E)
+    from paper_2106_13308_gb300.vqmc import DEVERR_NONFINITE
+    assert m.check() & DEVERR_NONFINITE
+    assert m.check() == 0  # cleared
+
+
+def test_invalid_batch_rejected():
+    from paper_2106_13308_gb300.vqmc import VQMCError
+    n, h, B = 30, 16, 8
+    m = make_model(n, h, B, er_instance(n, 0.2, 131))
+    with pytest.raises(VQMCError):
+        m.sample(B + 1)
+    with pytest.raises(VQMCError):
+        m.step(0)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_full_size_er10000_sampled_outputs(prec):
+    """The benchmark workload (G(10000, 8/9999), weights in {1..10}, h = 2000,
+    B = 2048) in the benchmark's launch configuration, checked on outputs the
+    oracle computes one by one: every energy (bit-exact), 6 samples
+    teacher-forced, their log pi, and the gradient of 4 samples."""
+    cfg = inputs.config("maxcut_er10000")
+    inst = inputs.make_instance(cfg)
+    n, h, B = cfg["n"], cfg["h"], cfg["B"]
+    theta = inputs.lively_params(n, h, cfg["param_seed"])
+    seed = 2024
+    m = make_model(n, h, B, inst, precision=prec, theta=theta, seed=seed)
+    P = oracle_params(theta, n, h, prec)
+    S, lp = m.sample(B, None, iteration=0)
+    E = m.local_energy(S).cpu().numpy()
+    Sn = S.cpu().numpy()
+    assert np.array_equal(E.astype(np.float64), oracle.energy(inst, Sn))
+    pick = np.array([0, 1, 777, 1024, 2046, 2047])
+    U = oracle.uniforms(B, n, seed, 0)[pick]
+    mism, ties = teacher_forced(P, Sn[pick], U, "relu")
+    assert mism == 0, (mism, ties)
+    lpo = oracle.logprob(P, Sn[pick])
+    assert logp_rel(lp.cpu().numpy()[pick], lpo) <= 1e-5
+    lpg = m.logprob(S).cpu().numpy()[pick]
+    assert logp_rel(lpg, lpo) <= (1e-5 if prec == "fp32" else 2e-2)
+    gout = np.zeros(B, dtype=np.float32)
+    gsel = pick[:4]
+    gout[gsel] = np.array([0.5, -1.0, 0.25, 2.0], dtype=np.float32)
+    g = m.logprob_backward(S, torch.from_numpy(gout).cuda()).cpu().numpy()
+    go = oracle.made_to_theta(*oracle.logprob_grad(P, Sn[gsel], gout[gsel].astype(np.float64)))
+    assert rel_err(g, go) <= (1e-4 if prec == "fp32" else 3e-2)
