@@ -27,17 +27,18 @@ __global__ void mask_kernel(int n, int h, float* __restrict__ theta) {
   }
 }
 
-// Row copies: wt_s[j][k] = W1^T[j][k], v_s[i][k] = W2[i][k], zero padding k >= h.
+// Row copies for the sampler: wt_s[j][k] = W1^T[j-1][k] (row 0 zero),
+// v_s[i][k] = W2[i][k]; zero for k >= h and for rows past the matrix.
 template <typename T>
-__global__ void rows_kernel(int n, int h, int hp, const float* __restrict__ theta, T* __restrict__ wt_s,
+__global__ void rows_kernel(int n, int h, int hp, int rows, const float* __restrict__ theta, T* __restrict__ wt_s,
                             T* __restrict__ v_s) {
   const float* W2 = theta + (long long)n * h + h;
-  const long long tot = (long long)n * hp;
+  const long long tot = (long long)rows * hp;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot; q += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(q / hp), k = (int)(q % hp);
     const bool in = k < h;
-    wt_s[q] = cvt<T>(in ? theta[(long long)r * h + k] : 0.0f);
-    v_s[q] = cvt<T>(in ? W2[(long long)r * h + k] : 0.0f);
+    wt_s[q] = cvt<T>(in && r >= 1 && r <= n ? theta[(long long)(r - 1) * h + k] : 0.0f);
+    v_s[q] = cvt<T>(in && r < n ? W2[(long long)r * h + k] : 0.0f);
   }
 }
 
@@ -90,8 +91,9 @@ int grid_for(long long work, int block = 256) {
 
 template <typename T>
 cudaError_t refresh(vqmc_ctx* c, cudaStream_t st) {
-  const long long nh = (long long)c->n * c->hp;
-  rows_kernel<T><<<grid_for(nh), 256, 0, st>>>(c->n, c->h, c->hp, c->theta, (T*)c->wt_s, (T*)c->v_s);
+  const int rows = sampler_rows(c->n);
+  rows_kernel<T><<<grid_for((long long)rows * c->hp), 256, 0, st>>>(c->n, c->h, c->hp, rows, c->theta, (T*)c->wt_s,
+                                                                    (T*)c->v_s);
   dim3 grid((c->np + 31) / 32, (c->h + 31) / 32), block(32, 8);
   transpose_kernel<T><<<grid, block, 0, st>>>(c->n, c->h, c->np, c->theta, (T*)c->w_s);
   transpose_kernel<T><<<grid, block, 0, st>>>(c->n, c->h, c->np, c->theta + (long long)c->n * c->h + c->h,

@@ -18,8 +18,11 @@ constexpr int kPad = 64;
 inline int pad_up(int x, int p = kPad) { return (x + p - 1) / p * p; }
 
 // MADE degree of hidden unit k (0-based): m(k) = 1 + floor(k (n-1) / h).
+// 32-bit arithmetic when k (n-1) fits (every size this library accepts).
 __host__ __device__ inline int degree(int k, int n, int h) {
-  return 1 + (int)(((long long)k * (long long)(n - 1)) / (long long)h);
+  const long long p = (long long)k * (long long)(n - 1);
+  if (p < (1ll << 32)) return 1 + (int)((unsigned)p / (unsigned)h);
+  return 1 + (int)(p / (long long)h);
 }
 
 // Number of hidden units whose degree is <= x, i.e. #{k : k (n-1) < x h}.
@@ -29,6 +32,11 @@ __host__ __device__ inline int count_deg_le(int x, int n, int h) {
   long long c = ((long long)x * h + (n - 2)) / (n - 1);
   return c > h ? h : (int)c;
 }
+
+// The sampler streams SPS consecutive rows per copy; its weight copies have
+// this many rows (wt_s row j = input j with row 0 zero, v_s row i = output i+1).
+constexpr int kSamplerRowsPad = 8;
+inline int sampler_rows(int n) { return (n + 1 + kSamplerRowsPad - 1) / kSamplerRowsPad * kSamplerRowsPad; }
 
 // Device error word bits mirror VQMC_DEVERR_*.
 constexpr uint32_t kErrTimeout = VQMC_DEVERR_TIMEOUT;
@@ -62,8 +70,10 @@ struct vqmc_ctx {
   uint64_t iter = 0;
 
   // Kernel-side weight copies, element type float (FP32) or bf16 (BF16):
-  //   wt_s [n][hp]  rows of W1^T (input j -> all units), sampler
-  //   v_s  [n][hp]  rows of W2 (output i <- all units), sampler and Z GEMM
+  //   wt_s [sampler_rows(n)][hp]  row j = column j of W1 (input j, 1-based),
+  //                               row 0 and rows > n zero; sampler
+  //   v_s  [sampler_rows(n)][hp]  row i = row i of W2 (output i+1), rows >= n
+  //                               zero; sampler and Z GEMM
   //   w_s  [h][np]  rows of W1 (unit k <- all inputs), hidden GEMM
   //   vt_s [h][np]  rows of W2^T (unit k -> all outputs), backward GEMM
   void* wt_s = nullptr;

@@ -12,9 +12,9 @@
 //       s_i = +1 iff u_{b,i} < sigma(z_i) for all samples of the CTA.
 // Each unit does exactly one multiply-add per step and sample (an update
 // while m(k) >= i, a dot term afterwards), so a sample costs h*n FMA.
-// Row i-1 of W1^T and row i of W2 are streamed into a shared-memory ring by
-// bulk asynchronous copies (cp.async.bulk + mbarrier transaction counts),
-// NSTAGE steps ahead of use.
+// Rows of W1^T and W2 are streamed into a shared-memory ring by bulk
+// asynchronous copies (cp.async.bulk + mbarrier transaction counts), SPS
+// consecutive rows of each per copy, several stages ahead of use.
 //
 // Lane layout: lane = 8*sg + ug.  The 8 "unit groups" ug of a warp hold 8
 // consecutive hidden units of each slot; the 4 "sample groups" sg hold SL
@@ -94,6 +94,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait: false (and the timeout bit set) if the phase never completed.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t* err) {
   for (long long it = 0; it < kSpinLimit; ++it)
@@ -109,13 +120,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 
 // ------------------------------------------------------------------ helpers
-
-template <typename T>
-__device__ __forceinline__ float ld_w(const T* p);
-template <>
-__device__ __forceinline__ float ld_w<float>(const float* p) { return *p; }
-template <>
-__device__ __forceinline__ float ld_w<bf16>(const bf16* p) { return __bfloat162float(*p); }
 
 template <typename T>
 __device__ __forceinline__ T from_f(float x);
@@ -137,8 +141,37 @@ __device__ __forceinline__ float log_sigmoid(float x) {
 
 constexpr int kBig = 0x3fffffff;
 
+// ---- packed FP32 pairs (fma.rn.f32x2: two IEEE FP32 FMAs in one instruction)
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// weights of units (2q, 2q+1) of a staged row as an FP32 pair
+template <typename T>
+__device__ __forceinline__ uint64_t ld_pair(const T* row, int q);
+template <>
+__device__ __forceinline__ uint64_t ld_pair<bf16>(const bf16* row, int q) {
+  const uint32_t x = reinterpret_cast<const uint32_t*>(row)[q];
+  return pack2(__uint_as_float(x << 16), __uint_as_float(x & 0xffff0000u));
+}
+template <>
+__device__ __forceinline__ uint64_t ld_pair<float>(const float* row, int q) {
+  return reinterpret_cast<const uint64_t*>(row)[q];
+}
+
 struct SamplerArgs {
   int n, h, hp, B;
+  int nst;          // ring stages
   const void* wt;   // [n][hp]
   const void* v;    // [n][hp]
   const float* b1;  // [h]
@@ -154,293 +187,389 @@ struct SamplerArgs {
   uint32_t* err;
 };
 
-template <typename WT, int NW, int UL, int SL, int ACT>
+// A CTA = NGRP groups of GW warps.  Group g owns
+// SL samples; its GW*32 lanes split the hidden units: lane L of the group
+// holds unit pairs q = r*GW*32 + L (units 2q, 2q+1), r = 0..U2-1, for all SL
+// samples.  Per step a group reduces its partial sums with shuffles and one
+// named barrier of its own warps; groups never wait for each other.  Lane 0
+// of the last warp also keeps the weight ring filled: whenever every warp
+// has released a stage it issues the copies for the block a full ring ahead.
+template <typename WT, int GW, int NGRP, int U2, int SL, int ACT>
 struct Sampler {
-  static constexpr int S = 4 * SL;           // samples per CTA
-  static constexpr int SLOTSTRIDE = 8 * NW;  // units between slots of a lane
-  static constexpr int RL = 8 * NW * UL;     // row length held in shared memory
-  static constexpr int NSTAGE = 8;
+  static constexpr int NCW = GW * NGRP;      // warps
+  static constexpr int NT = NCW * 32;        // threads
+  static constexpr int S = SL * NGRP;        // samples per CTA
+  static constexpr int GL = GW * 32;         // lanes per group
+  static constexpr int RL = GL * 2 * U2;     // units covered (row length in smem)
+  static constexpr int SPS = 4;              // steps per ring stage (rows per copy)
+  static constexpr int UWIN = 128 / SL;      // steps per uniform window (32 lanes x 4 words)
+  static_assert(SL >= 1 && SL <= 16 && (SL & (SL - 1)) == 0, "SL must be a power of two <= 16");
 
   struct State {
-    float a[UL][SL];
-    float acc[SL];
-    float sgn[SL];
+    uint64_t a[U2][SL];  // pre-activations of units (2q, 2q+1), or act() once complete
+    uint64_t acc[SL];    // dot accumulators (even / odd units)
+    uint64_t sg[SL];     // {s_{i-1}, s_{i-1}}
   };
 
-  // Slots r < ND: all units complete -> dot; slot ND: mixed (per lane);
-  // slots r > ND: all units still accumulating -> update.
-  template <int ND>
-  static __device__ __forceinline__ void body(State& st, const WT* __restrict__ wrow, const WT* __restrict__ vrow,
-                                              int kbase, int i, int m_gen) {
+  static __device__ __forceinline__ int deg(int k, int n, int h) { return k < h ? degree(k, n, h) : kBig; }
+
+  // Mixed slot: the lane's two units may be in different roles.  Weights of
+  // units that must not take part are zeroed, so the pair still runs as f32x2.
+  static __device__ __forceinline__ void mixed(State& st, const WT* wrow, const WT* vrow, int r, int q, int i,
+                                               int m0, int m1) {
+    if (i >= 2 && (m0 >= i - 1 || m1 >= i - 1)) {
+      float w0, w1;
+      unpack2(ld_pair(wrow, q), w0, w1);
+      const uint64_t w = pack2(m0 >= i - 1 ? w0 : 0.0f, m1 >= i - 1 ? w1 : 0.0f);
 #pragma unroll
-    for (int r = 0; r < ND && r < UL; ++r) {
-      const float w = ld_w(vrow + kbase + r * SLOTSTRIDE);
-#pragma unroll
-      for (int q = 0; q < SL; ++q) st.acc[q] = fmaf(w, st.a[r][q], st.acc[q]);
+      for (int s = 0; s < SL; ++s) st.a[r][s] = fma2(w, st.sg[s], st.a[r][s]);
     }
-    if constexpr (ND < UL) {
-      const int k = kbase + ND * SLOTSTRIDE;
-      if (i >= 2 && m_gen >= i - 1) {
-        const float w = ld_w(wrow + k);
+    if (m0 == i - 1 || m1 == i - 1) {
 #pragma unroll
-        for (int q = 0; q < SL; ++q) st.a[ND][q] = fmaf(w, st.sgn[q], st.a[ND][q]);
+      for (int s = 0; s < SL; ++s) {
+        float a0, a1;
+        unpack2(st.a[r][s], a0, a1);
+        if (m0 == i - 1) a0 = act_f<ACT>(a0);
+        if (m1 == i - 1) a1 = act_f<ACT>(a1);
+        st.a[r][s] = pack2(a0, a1);
       }
-      if (m_gen == i - 1) {
+    }
+    if (m0 <= i - 1) {
+      float v0, v1;
+      unpack2(ld_pair(vrow, q), v0, v1);
+      const uint64_t v = pack2(v0, m1 <= i - 1 ? v1 : 0.0f);
 #pragma unroll
-        for (int q = 0; q < SL; ++q) st.a[ND][q] = act_f<ACT>(st.a[ND][q]);
-      }
-      if (m_gen <= i - 1) {
-        const float w = ld_w(vrow + k);
+      for (int s = 0; s < SL; ++s) st.acc[s] = fma2(v, st.a[r][s], st.acc[s]);
+    }
+  }
+
+  // Slots r < ND: every unit complete -> dot.  MIX: slot ND is mixed.
+  // Remaining slots: every unit still accumulating -> update.
+  template <int ND, bool MIX>
+  static __device__ __forceinline__ void body(State& st, const WT* __restrict__ wrow, const WT* __restrict__ vrow,
+                                              int lq, int i, int m0, int m1) {
 #pragma unroll
-        for (int q = 0; q < SL; ++q) st.acc[q] = fmaf(w, st.a[ND][q], st.acc[q]);
-      }
-      if (i >= 2) {
+    for (int r = 0; r < ND && r < U2; ++r) {
+      const uint64_t w = ld_pair(vrow, lq + r * GL);
 #pragma unroll
-        for (int r = ND + 1; r < UL; ++r) {
-          const float w = ld_w(wrow + kbase + r * SLOTSTRIDE);
+      for (int s = 0; s < SL; ++s) st.acc[s] = fma2(w, st.a[r][s], st.acc[s]);
+    }
+    constexpr int FIRST_UPD = MIX ? ND + 1 : ND;
+    if constexpr (MIX && ND < U2) mixed(st, wrow, vrow, ND, lq + ND * GL, i, m0, m1);
+    if (i >= 2) {
 #pragma unroll
-          for (int q = 0; q < SL; ++q) st.a[r][q] = fmaf(w, st.sgn[q], st.a[r][q]);
-        }
+      for (int r = FIRST_UPD; r < U2; ++r) {
+        const uint64_t w = ld_pair(wrow, lq + r * GL);
+#pragma unroll
+        for (int s = 0; s < SL; ++s) st.a[r][s] = fma2(w, st.sg[s], st.a[r][s]);
       }
     }
   }
 
+  // code = 2*nd + mixed, nd in [0, U2]
   template <int LO, int HI>
-  static __device__ __forceinline__ void dispatch(int nd, State& st, const WT* wrow, const WT* vrow, int kbase,
-                                                  int i, int m_gen) {
+  static __device__ __forceinline__ void dispatch(int code, State& st, const WT* wrow, const WT* vrow, int lq, int i,
+                                                  int m0, int m1) {
     if constexpr (LO == HI) {
-      body<LO>(st, wrow, vrow, kbase, i, m_gen);
+      body<LO / 2, (LO & 1) != 0>(st, wrow, vrow, lq, i, m0, m1);
     } else {
       constexpr int MID = (LO + HI) / 2;
-      if (nd <= MID) dispatch<LO, MID>(nd, st, wrow, vrow, kbase, i, m_gen);
-      else dispatch<MID + 1, HI>(nd, st, wrow, vrow, kbase, i, m_gen);
+      if (code <= MID) dispatch<LO, MID>(code, st, wrow, vrow, lq, i, m0, m1);
+      else dispatch<MID + 1, HI>(code, st, wrow, vrow, lq, i, m0, m1);
     }
   }
 
-  // Fallback when more than one slot of the warp is mixed (tiny n / large h).
-  static __device__ __forceinline__ void body_general(State& st, const WT* __restrict__ wrow,
-                                                      const WT* __restrict__ vrow, int kbase, int i, int n,
-                                                      int h) {
+  // every slot treated as mixed (small n or h >> n)
+  static __device__ __forceinline__ void body_general(State& st, const WT* wrow, const WT* vrow, int lq, int i,
+                                                      int n, int h) {
 #pragma unroll
-    for (int r = 0; r < UL; ++r) {
-      const int k = kbase + r * SLOTSTRIDE;
-      const int m = k < h ? degree(k, n, h) : kBig;
-      if (i >= 2 && m >= i - 1) {
-        const float w = ld_w(wrow + k);
-#pragma unroll
-        for (int q = 0; q < SL; ++q) st.a[r][q] = fmaf(w, st.sgn[q], st.a[r][q]);
-      }
-      if (m == i - 1) {
-#pragma unroll
-        for (int q = 0; q < SL; ++q) st.a[r][q] = act_f<ACT>(st.a[r][q]);
-      }
-      if (m <= i - 1) {
-        const float w = ld_w(vrow + k);
-#pragma unroll
-        for (int q = 0; q < SL; ++q) st.acc[q] = fmaf(w, st.a[r][q], st.acc[q]);
-      }
+    for (int r = 0; r < U2; ++r) {
+      const int q = lq + r * GL;
+      mixed(st, wrow, vrow, r, q, i, deg(2 * q, n, h), deg(2 * q + 1, n, h));
     }
   }
 
-  static __device__ __forceinline__ int deg_or_big(int k, int n, int h) { return k < h ? degree(k, n, h) : kBig; }
+  // Reduce SL values over the 32 lanes: afterwards lane l holds the warp sum
+  // of sample q(l); lanes with (l & (32/SL - 1)) == 0 hold distinct samples.
+  static __device__ __forceinline__ float reduce_scatter(float (&v)[SL], int lane, int& q) {
+    q = 0;
+    int cnt = SL;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      if (cnt > 1) {
+        const bool up = (lane & o) != 0;
+        const int half = cnt / 2;
+#pragma unroll
+        for (int e = 0; e < SL / 2; ++e) {
+          if (e < half) {
+            const float keep = up ? v[e + half] : v[e];
+            const float send = up ? v[e] : v[e + half];
+            v[e] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+          }
+        }
+        q = 2 * q + (up ? 1 : 0);
+        cnt = half;
+      } else {
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+      }
+    }
+    return v[0];
+  }
 
-  static size_t smem_bytes() {
-    return (size_t)NSTAGE * 2 * RL * sizeof(WT) + 128 + (size_t)2 * NW * S * sizeof(float) + 64;
+  // ring stages (each: SPS rows of W1^T and SPS rows of W2) that fit the
+  // shared-memory budget, at most 8
+  static int stages_for(int hp) {
+    const size_t stage = (size_t)2 * SPS * hp * sizeof(WT);
+    const size_t fixed = (size_t)RL * sizeof(WT) + 2 * 8 * 8 + (size_t)2 * NGRP * GW * SL * sizeof(float) + 256;
+    int nst = (int)((200 * 1024 - fixed) / stage);
+    return nst > 8 ? 8 : nst;
+  }
+  static size_t smem_bytes(int hp, int nst) {
+    return (size_t)nst * 2 * SPS * hp * sizeof(WT) + (size_t)RL * sizeof(WT) + 2 * 8 * 8 +
+           (size_t)2 * NGRP * GW * SL * sizeof(float) + 64;
   }
 };
 
-template <typename WT, int NW, int UL, int SL, int ACT>
-__global__ void __launch_bounds__(NW * 32, 1) sampler_kernel(const SamplerArgs g) {
-  using K = Sampler<WT, NW, UL, SL, ACT>;
-  constexpr int S = K::S, RL = K::RL, NSTAGE = K::NSTAGE;
+template <typename WT, int GW, int NGRP, int U2, int SL, int ACT>
+__global__ void __launch_bounds__(GW * NGRP * 32, 1) sampler_kernel(const SamplerArgs g) {
+  using K = Sampler<WT, GW, NGRP, U2, SL, ACT>;
+  constexpr int RL = K::RL, SPS = K::SPS, NCW = K::NCW, GL = K::GL, UWIN = K::UWIN;
   extern __shared__ __align__(128) unsigned char smem[];
+  const int nst = g.nst, hp = g.hp;
+  const int stage_elems = 2 * SPS * hp;  // W1^T rows then W2 rows
+  // ring, then RL elements of slack: lanes holding padding units (k >= hp)
+  // read past their row, never past the ring
+  const int ring_elems = nst * stage_elems + RL;
   WT* stages = reinterpret_cast<WT*>(smem);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)NSTAGE * 2 * RL * sizeof(WT));
-  uint64_t* redbar = full + NSTAGE;
-  float* red = reinterpret_cast<float*>(full + NSTAGE + 2);  // [2][NW][S]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + ((size_t)ring_elems * sizeof(WT) + 7) / 8 * 8);
+  uint64_t* empty = full + 8;
+  float* red = reinterpret_cast<float*>(empty + 8);  // [2][NGRP][GW][SL]
 
   const int n = g.n, h = g.h;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int sg = lane >> 3, ug = lane & 7;
-  const int b0 = blockIdx.x * S;
   const uint32_t FULL = 0xffffffffu;
 
-  // zero the row tails beyond the copied hp elements (never overwritten)
-  for (int q = tid; q < NSTAGE * 2 * (RL - g.hp); q += NW * 32) {
-    const int row = q / (RL - g.hp), col = q % (RL - g.hp);
-    stages[(size_t)row * RL + g.hp + col] = from_f<WT>(0.0f);
-  }
+  // zero the ring once: every value a lane may read must be finite
+  for (int q = tid; q < ring_elems; q += K::NT) stages[q] = from_f<WT>(0.0f);
   if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) mbar_init(smem_u32(&full[s]), 1);
-    mbar_init(smem_u32(redbar), NW * 32);
+    for (int s = 0; s < nst; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), NCW);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
 
-  const uint32_t row_bytes = (uint32_t)(g.hp * sizeof(WT));
+  // ------------------------------------------------------------ producer
+  const bool producer = warp == NCW - 1 && lane == 0;
   const WT* gwt = reinterpret_cast<const WT*>(g.wt);
   const WT* gv = reinterpret_cast<const WT*>(g.v);
-  // Stage for step j (1-based): W1^T row j-2 (input j-1, j >= 2) and W2 row j-1.
-  auto issue = [&](int j) {
-    const int s = (j - 1) % NSTAGE;
+  const int nblocks = (n + SPS - 1) / SPS;
+  int issued = 0;  // ring blocks (SPS steps each) whose copies were issued (producer lane)
+  // Block q covers steps q*SPS+1 .. q*SPS+SPS: rows q*SPS.. of wt_s (row j =
+  // input j, row 0 zero) and of v_s (row i = output i+1), copied whole.
+  const uint32_t block_bytes = (uint32_t)(SPS * hp * sizeof(WT));
+  auto issue = [&](int q) {
+    const int s = q % nst;
     const uint32_t bar = smem_u32(&full[s]);
-    WT* dst = stages + (size_t)s * 2 * RL;
-    mbar_expect_tx(bar, (j >= 2 ? row_bytes : 0u) + row_bytes);
-    if (j >= 2) bulk_g2s(smem_u32(dst), gwt + (size_t)(j - 2) * g.hp, row_bytes, bar);
-    bulk_g2s(smem_u32(dst + RL), gv + (size_t)(j - 1) * g.hp, row_bytes, bar);
+    WT* dst = stages + (size_t)s * stage_elems;
+    mbar_expect_tx(bar, 2 * block_bytes);
+    bulk_g2s(smem_u32(dst), gwt + (size_t)q * SPS * hp, block_bytes, bar);
+    bulk_g2s(smem_u32(dst + SPS * hp), gv + (size_t)q * SPS * hp, block_bytes, bar);
+    issued = q + 1;
   };
-  int issued = 0, consumed = 0;  // steps whose copies were issued / waited for (thread 0)
-  if (tid == 0)
-    for (int j = 1; j <= n && j <= NSTAGE; ++j) issue(j), issued = j;
+  // refill every stage all warps have released (non-blocking)
+  auto refill = [&]() {
+    while (issued < nblocks) {
+      const int q = issued;
+      if (q >= nst && !mbar_test_wait(smem_u32(&empty[q % nst]), (uint32_t)((q / nst - 1) & 1))) break;
+      issue(q);
+    }
+  };
+  if (producer) refill();
+
+  // ----------------------------------------------------------- consumers
+  const int grp = warp / GW, wg = warp % GW;
+  const int L = wg * 32 + lane;                  // lane within the group
+  const int b0 = blockIdx.x * K::S + grp * SL;   // first sample of the group
+  float* gred = red + (size_t)grp * GW * SL;     // + buf * NGRP*GW*SL
 
   typename K::State st;
-  const int kbase = 8 * warp + ug;
 #pragma unroll
-  for (int r = 0; r < UL; ++r) {
-    const int k = kbase + r * K::SLOTSTRIDE;
-    const float bk = k < h ? g.b1[k] : 0.0f;
+  for (int r = 0; r < U2; ++r) {
+    const int k = 2 * (r * GL + L);
+    const float x0 = k < h ? __ldg(g.b1 + k) : 0.0f;
+    const float x1 = k + 1 < h ? __ldg(g.b1 + k + 1) : 0.0f;
 #pragma unroll
-    for (int q = 0; q < SL; ++q) st.a[r][q] = bk;
+    for (int s = 0; s < SL; ++s) st.a[r][s] = pack2(x0, x1);
   }
 #pragma unroll
-  for (int q = 0; q < SL; ++q) st.sgn[q] = 0.0f;
+  for (int s = 0; s < SL; ++s) st.sg[s] = pack2(0.0f, 0.0f);
 
-  // warp-uniform slot bookkeeping
-  const int k7 = 8 * warp + 7, k0 = 8 * warp;
+  // warp-uniform slot bookkeeping: nd = #slots complete before this step,
+  // nt = #slots with at least one unit complete at this step
+  const int kw = 2 * wg * 32;  // first unit of the warp in slot 0
   int nd = 0, nt = 0;
-  int thr_nd = K::deg_or_big(k7, n, h), thr_nt = K::deg_or_big(k0, n, h);
-  int m_gen = K::deg_or_big(kbase, n, h);
+  int thr_nd = K::deg(kw + 63, n, h), thr_nt = K::deg(kw, n, h);
+  int m0 = K::deg(2 * L, n, h), m1 = K::deg(2 * L + 1, n, h);
 
-  // per-sample inputs for the draw (lanes < S)
-  const int my_b = b0 + (lane < S ? lane : 0);
-  const bool my_valid = lane < S && my_b < g.B;
-  float ucur[4] = {0.5f, 0.5f, 0.5f, 0.5f}, unxt[4] = {0.5f, 0.5f, 0.5f, 0.5f};
-  const float* urow = g.u ? g.u + (size_t)my_b * n : nullptr;
-  if (urow && my_valid)
-    for (int e = 0; e < 4 && e < n; ++e) unxt[e] = __ldg(urow + e);
-  float cval = __ldg(g.b2);
+  // uniforms: lane L (< 32) holds 4 words for sample L % SL, steps
+  // win + 4*(L / SL) .. +3 of the current window
+  const int us = lane % SL, ug = lane / SL;
+  const int ub = b0 + us;
+  const bool uvalid = ub < g.B;
+  uint32_t uw[4] = {0, 0, 0, 0}, unx[4] = {0, 0, 0, 0};
+  auto load_u = [&](int win, uint32_t (&dst)[4]) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int t = win + 4 * ug + e;
+      dst[e] = (uvalid && t < n) ? __float_as_uint(__ldg(g.u + (size_t)ub * n + t)) : 0x3f000000u;
+    }
+  };
+  if (g.u) load_u(0, unx);
+  float cw = lane < n ? __ldg(g.b2 + lane) : 0.0f, cnx = 0.0f;
+  if (32 + lane < n) cnx = __ldg(g.b2 + 32 + lane);
+
+  const bool writer = wg == 0 && lane < SL && b0 + lane < g.B;
+  const int my_b = b0 + lane;
   float lp = 0.0f;
   bool ok = true;
   WT* sx = reinterpret_cast<WT*>(g.sx);
   WT* stt = reinterpret_cast<WT*>(g.st);
 
+  int cs = 0;         // ring stage of the current block
+  uint32_t cpar = 0;  // phase parity of that stage's current fill
   for (int i = 1; i <= n; ++i) {
     const int t = i - 1;
-    // uniforms for steps t..t+3
-    if ((t & 3) == 0) {
-      if (urow) {
+    if (t % UWIN == 0) {
+      if (g.u) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) ucur[e] = unxt[e];
-        if (my_valid) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (t + 4 + e < n) unxt[e] = __ldg(urow + t + 4 + e);
-        }
+        for (int e = 0; e < 4; ++e) uw[e] = unx[e];
+        if (t + UWIN < n) load_u(t + UWIN, unx);
       } else {
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)(t >> 2), (uint32_t)my_b, g.it0, g.it1), g.key0, g.key1);
-        ucur[0] = to_unit(r.x);
-        ucur[1] = to_unit(r.y);
-        ucur[2] = to_unit(r.z);
-        ucur[3] = to_unit(r.w);
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)((t + 4 * ug) >> 2), (uint32_t)ub, g.it0, g.it1), g.key0,
+                                      g.key1);
+        uw[0] = r.x, uw[1] = r.y, uw[2] = r.z, uw[3] = r.w;
       }
     }
-    const float cnext = (i < n) ? __ldg(g.b2 + i) : 0.0f;
-
-    // slot bookkeeping (warp-uniform)
-    while (nd < UL && thr_nd <= i - 2) {
+    if ((t & 31) == 0 && t > 0) {
+      cw = cnx;
+      cnx = (t + 32 + lane < n) ? __ldg(g.b2 + t + 32 + lane) : 0.0f;
+    }
+    while (nd < U2 && thr_nd <= i - 2) {
       ++nd;
-      thr_nd = nd < UL ? K::deg_or_big(k7 + nd * K::SLOTSTRIDE, n, h) : kBig;
-      m_gen = nd < UL ? K::deg_or_big(kbase + nd * K::SLOTSTRIDE, n, h) : kBig;
+      thr_nd = nd < U2 ? K::deg(kw + nd * 2 * GL + 63, n, h) : kBig;
+      m0 = nd < U2 ? K::deg(2 * (L + nd * GL), n, h) : kBig;
+      m1 = nd < U2 ? K::deg(2 * (L + nd * GL) + 1, n, h) : kBig;
     }
-    while (nt < UL && thr_nt <= i - 1) {
+    while (nt < U2 && thr_nt <= i - 1) {
       ++nt;
-      thr_nt = nt < UL ? K::deg_or_big(k0 + nt * K::SLOTSTRIDE, n, h) : kBig;
+      thr_nt = nt < U2 ? K::deg(kw + nt * 2 * GL, n, h) : kBig;
     }
 
-    const int s = t % NSTAGE;
-    if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((t / NSTAGE) & 1), g.err)) {
-      ok = false;
-      break;
+    const int ro = t % SPS;
+    if (ro == 0 && t > 0 && ++cs == nst) cs = 0, cpar ^= 1u;
+    const int s = cs;
+    if (ro == 0) {
+      const uint32_t fb = smem_u32(&full[s]), par = cpar;
+      bool got = false;
+      if (warp == NCW - 1) {
+        // the producer's warp never suspends: lane 0 keeps refilling
+        for (long long it = 0; it < kSpinLimit && !got; ++it) {
+          if (producer) refill();
+          got = mbar_test_wait(fb, par);
+        }
+      } else {
+        for (long long it = 0; it < kSpinLimit && !got; ++it) got = mbar_try_wait(fb, par);
+      }
+      if (!got) {
+        atomicOr(g.err, kErrTimeout);
+        ok = false;
+        break;
+      }
     }
-    consumed = i;
-    const WT* wrow = stages + (size_t)s * 2 * RL;
-    const WT* vrow = wrow + RL;
+    const WT* wrow = stages + (size_t)s * stage_elems + ro * hp;
+    const WT* vrow = wrow + SPS * hp;
 #pragma unroll
-    for (int q = 0; q < SL; ++q) st.acc[q] = 0.0f;
-    if (nt <= nd + 1) K::template dispatch<0, UL>(nd, st, wrow, vrow, kbase, i, m_gen);
-    else K::body_general(st, wrow, vrow, kbase, i, n, h);
+    for (int q = 0; q < SL; ++q) st.acc[q] = pack2(0.0f, 0.0f);
+    if (nt <= nd + 1) K::template dispatch<0, 2 * U2>(2 * nd + (nt - nd), st, wrow, vrow, L, i, m0, m1);
+    else K::body_general(st, wrow, vrow, L, i, n, h);
+    if (ro == SPS - 1 || i == n) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+    }
 
-    // lane reduction over the 8 unit groups; lane ug == q keeps sample q
-    const int buf = t & 1;
+    // z_i: lanes -> warp (shuffles) -> group (shared memory + named barrier)
+    float v[SL];
 #pragma unroll
     for (int q = 0; q < SL; ++q) {
-      float v = st.acc[q];
-      v += __shfl_xor_sync(FULL, v, 1);
-      v += __shfl_xor_sync(FULL, v, 2);
-      v += __shfl_xor_sync(FULL, v, 4);
-      if (ug == q) red[(buf * NW + warp) * S + sg * SL + q] = v;
+      float lo, hi;
+      unpack2(st.acc[q], lo, hi);
+      v[q] = lo + hi;
     }
-    mbar_arrive(smem_u32(redbar));
-    if (!mbar_wait(smem_u32(redbar), (uint32_t)(t & 1), g.err)) {
-      ok = false;
-      break;
-    }
-    // stage s is free: every thread has finished reading it
-    if (tid == 0 && i + NSTAGE <= n) issue(i + NSTAGE), issued = i + NSTAGE;
-
-    // every warp draws s_i for all S samples (identical arithmetic)
-    float z = cval;
-    if (lane < S) {
+    int qs;
+    const float ws = K::reduce_scatter(v, lane, qs);
+    float* rb = gred + (size_t)(t & 1) * NGRP * GW * SL;
+    if ((lane & (32 / SL - 1)) == 0) rb[wg * SL + qs] = ws;
+    if constexpr (GW > 1) asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(GW * 32) : "memory");
+    else __syncwarp();
+    float z = __shfl_sync(FULL, cw, t & 31);
+    if (lane < SL) {
 #pragma unroll
-      for (int w = 0; w < NW; ++w) z += red[(buf * NW + w) * S + lane];
+      for (int w = 0; w < GW; ++w) z += rb[w * SL + lane];
     }
+    const int src = ((t % UWIN) >> 2) * SL + (lane < SL ? lane : 0);
+    const int e = t & 3;
+    const uint32_t wsel = e == 0 ? uw[0] : e == 1 ? uw[1] : e == 2 ? uw[2] : uw[3];
+    const uint32_t uword = __shfl_sync(FULL, wsel, src);
+    const float u = g.u ? __uint_as_float(uword) : to_unit(uword);
     const float p = 1.0f / (1.0f + expf(-z));
-    const float u = (t & 3) == 0 ? ucur[0] : (t & 3) == 1 ? ucur[1] : (t & 3) == 2 ? ucur[2] : ucur[3];
-    const bool up = lane < S && u < p;
+    const bool up = u < p;
     const uint32_t mask = __ballot_sync(FULL, up);
 #pragma unroll
-    for (int q = 0; q < SL; ++q) st.sgn[q] = ((mask >> (sg * SL + q)) & 1u) ? 1.0f : -1.0f;
-    if (warp == 0 && my_valid) {
-      lp += log_sigmoid(up ? z : -z);
+    for (int q = 0; q < SL; ++q) {
+      const float sv = ((mask >> q) & 1u) ? 1.0f : -1.0f;
+      st.sg[q] = pack2(sv, sv);
+    }
+    if (writer) {
       const float sv = up ? 1.0f : -1.0f;
+      if (g.logp) lp += log_sigmoid(up ? z : -z);
       g.s_out[(size_t)my_b * n + t] = up ? (int8_t)1 : (int8_t)-1;
       if (sx) sx[(size_t)my_b * g.ldsx + t] = from_f<WT>(sv);
       if (stt) stt[(size_t)t * g.ldst + my_b] = from_f<WT>(sv);
     }
-    cval = cnext;
   }
-
-  if (!ok) {
-    // Drain: the producer waits (bounded) for every copy it issued and no
-    // thread consumed, so no bulk copy is in flight when the CTA exits.
-    if (tid == 0)
-      for (int j = consumed + 1; j <= issued; ++j)
-        if (!mbar_wait(smem_u32(&full[(j - 1) % NSTAGE]), (uint32_t)(((j - 1) / NSTAGE) & 1), g.err)) break;
-    return;
+  if (!ok && producer) {
+    // drain: wait (bounded) for every copy still in flight before exiting
+    for (int q = issued - nst > 0 ? issued - nst : 0; q < issued; ++q)
+      if (!mbar_wait(smem_u32(&full[q % nst]), (uint32_t)((q / nst) & 1), g.err)) break;
   }
-  if (warp == 0 && my_valid && g.logp) g.logp[my_b] = lp;
+  if (ok && writer && g.logp) g.logp[my_b] = lp;
 }
 
-template <typename WT, int NW, int UL, int SL, int ACT>
+template <typename WT, int GW, int NGRP, int U2, int SL, int ACT>
 cudaError_t launch_cfg(const SamplerArgs& a, cudaStream_t st) {
-  using K = Sampler<WT, NW, UL, SL, ACT>;
-  const size_t smem = K::smem_bytes();
-  auto kern = sampler_kernel<WT, NW, UL, SL, ACT>;
+  using K = Sampler<WT, GW, NGRP, U2, SL, ACT>;
+  SamplerArgs b = a;
+  b.nst = K::stages_for(a.hp);
+  if (b.nst < 2) return cudaErrorNotSupported;
+  const size_t smem = K::smem_bytes(a.hp, b.nst);
+  auto kern = sampler_kernel<WT, GW, NGRP, U2, SL, ACT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = (a.B + K::S - 1) / K::S;
-  kern<<<grid, NW * 32, smem, st>>>(a);
+  kern<<<grid, K::NT, smem, st>>>(b);
   return cudaGetLastError();
 }
 
 template <typename WT, int ACT>
 cudaError_t launch_shape(const SamplerArgs& a, cudaStream_t st) {
-  // rows held in shared memory must cover hp = pad64(h)
-  if (a.hp <= 64) return launch_cfg<WT, 1, 8, 4, ACT>(a, st);
-  if (a.hp <= 512) return launch_cfg<WT, 8, 8, 4, ACT>(a, st);
-  if (a.hp <= 1024) return launch_cfg<WT, 8, 16, 4, ACT>(a, st);
-  if (a.hp <= 2048) return launch_cfg<WT, 8, 32, 4, ACT>(a, st);
+  // units covered by a group (GW*32 lanes x 2*U2) must be >= hp
+  if (a.hp <= 64) return launch_cfg<WT, 1, 2, 1, 8, ACT>(a, st);
+  if (a.hp <= 512) return launch_cfg<WT, 1, 2, 8, 8, ACT>(a, st);
+  if (a.hp <= 1024) return launch_cfg<WT, 2, 2, 8, 8, ACT>(a, st);
+  if (a.hp <= 2048) return launch_cfg<WT, 2, 4, 16, 4, ACT>(a, st);
   return cudaErrorNotSupported;
 }
 

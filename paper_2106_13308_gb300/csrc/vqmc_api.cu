@@ -224,8 +224,8 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
   VQ_ALLOC(c->grad, c->d * 4);
   c->b1 = c->theta + (size_t)n * h;
   c->b2 = c->theta + (size_t)2 * n * h + h;
-  VQ_ALLOC(c->wt_s, (size_t)n * c->hp * es);
-  VQ_ALLOC(c->v_s, (size_t)n * c->hp * es);
+  VQ_ALLOC(c->wt_s, (size_t)sampler_rows(n) * c->hp * es);
+  VQ_ALLOC(c->v_s, (size_t)sampler_rows(n) * c->hp * es);
   VQ_ALLOC(c->w_s, (size_t)h * c->np * es);
   VQ_ALLOC(c->vt_s, (size_t)h * c->np * es);
 
