@@ -41,6 +41,7 @@ struct GemmArgs {
   int ldr;
   float* col_part;     // [M-tile][ldc]
   int ldc;
+  uint32_t* err;       // device error word (bounded waits)
 };
 
 // K-range [lo, hi) of the N-tile [n0, n1) (clamped to N) for op.
@@ -76,7 +77,6 @@ __host__ __device__ inline bool gemm_out_kept(int op, int m, int k, int n, int h
 }
 
 cudaError_t launch_gemm_simt_f32(const GemmArgs<float>& a, cudaStream_t st);
-cudaError_t launch_gemm_simt_bf16(const GemmArgs<bf16>& a, cudaStream_t st);
 // tcgen05 path (BF16 operands, FP32 accumulation in tensor memory).
 cudaError_t launch_gemm_tc_bf16(const GemmArgs<bf16>& a, cudaStream_t st);
 bool gemm_tc_available();

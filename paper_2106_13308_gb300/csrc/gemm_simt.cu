@@ -1,6 +1,6 @@
-// CUDA-core (FFMA) implementation of the masked GEMMs with fused epilogues.
-// This is the "plain FP32" path (FP32 operands, FP32 accumulation) and the
-// reference implementation the tcgen05 path is compared against.
+// CUDA-core (FFMA) implementation of the masked GEMMs with fused epilogues:
+// the plain FP32 precision (FP32 operands, FP32 accumulation).  The BF16
+// precision runs the same GEMMs on the tcgen05 tensor cores (gemm_tc.cu).
 //
 // Tile 128 x 128 x 16, 256 threads, 8 x 8 outputs per thread (rows
 // m0 + 8*ty + i, columns n0 + 8*tx + j), register-staged double buffering.
@@ -257,6 +257,5 @@ cudaError_t launch_simt(const GemmArgs<T>& a, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_gemm_simt_f32(const GemmArgs<float>& a, cudaStream_t st) { return launch_simt(a, st); }
-cudaError_t launch_gemm_simt_bf16(const GemmArgs<bf16>& a, cudaStream_t st) { return launch_simt(a, st); }
 
 }  // namespace vqmc

@@ -1,10 +1,394 @@
-// tcgen05 tensor-core GEMM (BF16 operands, FP32 accumulation in tensor memory).
+// tcgen05 tensor-core implementation of the masked GEMMs (BF16 operands, FP32
+// accumulation in tensor memory) with the same fused epilogues as the
+// CUDA-core path (gemm_simt.cu).  Used for every GEMM of the BF16 precision:
+// the log-prob forward (Sec. 2.3), its adjoint (gradient of Sec. 2.1) and the
+// dense local energy.
+//
+// One CTA computes one 128 x 128 output tile with 4 warps:
+//   warp 0 allocates 128 TMEM columns; its lane 0 streams K-tiles of A
+//          (128 x 64) and B (128 x 64) into a 3-stage shared-memory ring with
+//          TMA (cp.async.bulk.tensor, 128-byte swizzle, zero fill beyond the
+//          tensor), mbarrier transaction counts marking each stage full;
+//   warp 1 lane 0 issues tcgen05.mma (M = 128, N = 128, K = 16, four per
+//          K-tile) into the TMEM accumulator and tcgen05.commit-s each stage
+//          back to the producer and, after the last K-tile, to the epilogue;
+//   all 4 warps read the accumulator with tcgen05.ld (warp w owns TMEM lanes
+//          32w..32w+31 = tile rows) and run the op's epilogue.
+// With ~100 KB of shared memory two CTAs share an SM, so one CTA's epilogue
+// overlaps the other's main loop.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "gemm.cuh"
 
 namespace vqmc {
+namespace {
 
-bool gemm_tc_available() { return false; }
+constexpr int BM = 128, BN = 128, BK = 64, NSTAGE = 3;
+constexpr int TILE_A_BYTES = BM * BK * 2;  // 16 KB
+constexpr int TILE_B_BYTES = BN * BK * 2;  // 16 KB
+constexpr int STAGE_BYTES = TILE_A_BYTES + TILE_B_BYTES;
+constexpr int TMEM_COLS = BN;  // FP32 accumulator: 128 lanes x BN columns
+constexpr int SMEM_BYTES = 1024 /*alignment slack*/ + NSTAGE * STAGE_BYTES + 256 /*barriers*/ + 4 * BN * 4;
 
-cudaError_t launch_gemm_tc_bf16(const GemmArgs<bf16>&, cudaStream_t) { return cudaErrorNotSupported; }
+// ------------------------------------------------------------------ PTX
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t* err) {
+  for (long long it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  if (err) atomicOr(err, kErrTimeout);
+  return false;
+}
+
+// 2D tiled TMA load: box at (x = inner/K element, y = row) into smem, completing
+// transaction bytes on bar.  x is always a multiple of 64 elements.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// UMMA shared-memory descriptor of a K-major operand tile written by TMA with
+// 128-byte swizzle: rows of 128 bytes (64 BF16 along K), 8-row groups 1024
+// bytes apart (stride byte offset), leading byte offset unused (1), version 1
+// (bits 46-47), layout SWIZZLE_128B (2, bits 61-63).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+__device__ __forceinline__ float log_sigmoidf_(float x) {
+  return x >= 0.0f ? -log1pf(expf(-x)) : x - log1pf(expf(x));
+}
+
+// Sum of v over the 32 lanes for 16 columns by recursive halving: afterwards
+// lane l holds the warp's sum of column colsum16_col(l) (lanes 2c and 2c+1
+// hold the same value).
+__device__ __forceinline__ float colsum16(float (&v)[16], int lane) {
+  float x[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const bool up = lane & 16;
+    const float keep = up ? v[e + 8] : v[e], send = up ? v[e] : v[e + 8];
+    x[e] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float y[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const bool up = lane & 8;
+    const float keep = up ? x[e + 4] : x[e], send = up ? x[e] : x[e + 4];
+    y[e] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float z[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const bool up = lane & 4;
+    const float keep = up ? y[e + 2] : y[e], send = up ? y[e] : y[e + 2];
+    z[e] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  const bool up = lane & 2;
+  float w = (up ? z[1] : z[0]) + __shfl_xor_sync(0xffffffffu, up ? z[0] : z[1], 2);
+  w += __shfl_xor_sync(0xffffffffu, w, 1);
+  return w;  // column index within the chunk: 8*b4 + 4*b3 + 2*b2 + b1 of the lane
+}
+__device__ __forceinline__ int colsum16_col(int lane) {
+  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
+__global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                      const __grid_constant__ CUtensorMap mapB,
+                                                      const __grid_constant__ CUtensorMap mapB2, const GemmArgs<bf16> g,
+                                                      int two_pass) {
+  uint32_t* err = g.err;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned tiles (128B swizzle atoms)
+  unsigned char* smem = smem_raw + (base - raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);
+  uint64_t* empty = full + NSTAGE;
+  uint64_t* done = empty + NSTAGE;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  float* colbuf = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES + 256);  // [4][BN]
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int op = g.op;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int m1 = min(m0 + BM, g.M), n1 = min(n0 + BN, g.N);
+
+  // fully masked weight-gradient tiles: zeros, no main loop
+  if ((op == kOpDV || op == kOpDW) && gemm_tile_masked(op, m0, m1, n0, n1, g.n, g.h)) {
+    for (int q = tid; q < BM * BN; q += 128) {
+      const int m = m0 + q / BN, nn = n0 + q % BN;
+      if (m < g.M && nn < g.N) g.gout[(size_t)m * g.ldg + nn] = 0.0f;
+    }
+    return;
+  }
+  int klo, khi;
+  gemm_k_range(op, n0, n1, g.K, g.n, g.h, &klo, &khi);
+  const int kt0 = klo / BK;
+  const int kt1 = (khi + BK - 1) / BK;
+  const int per_pass = kt1 > kt0 ? kt1 - kt0 : 0;
+  const int nkt = per_pass * (two_pass ? 2 : 1);
+
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------- producer
+    for (int it = 0; it < nkt && ok; ++it) {
+      const int s = it % NSTAGE;
+      if (it >= NSTAGE) ok = mbar_wait(smem_u32(&empty[s]), (uint32_t)((it / NSTAGE - 1) & 1), err);
+      if (!ok) break;
+      const int pass = it / per_pass, kt = kt0 + (it - pass * per_pass);
+      const uint32_t sa = base + s * STAGE_BYTES, sb = sa + TILE_A_BYTES;
+      const uint32_t bar = smem_u32(&full[s]);
+      mbar_expect_tx(bar, STAGE_BYTES);
+      tma_load_2d(sa, &mapA, kt * BK, m0, bar);
+      tma_load_2d(sb, pass == 0 ? &mapB : &mapB2, kt * BK, n0, bar);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // --------------------------------------------------------- MMA issuer
+    for (int it = 0; it < nkt && ok; ++it) {
+      const int s = it % NSTAGE;
+      ok = mbar_wait(smem_u32(&full[s]), (uint32_t)((it / NSTAGE) & 1), err);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t sa = base + s * STAGE_BYTES, sb = sa + TILE_A_BYTES;
+      const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k)  // advance 16 BF16 = 32 bytes along K inside the swizzle atom
+        mma_bf16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), (it > 0 || k > 0) ? 1u : 0u);
+      mma_commit(smem_u32(&empty[s]));
+    }
+    if (nkt > 0 && ok) mma_commit(smem_u32(done));
+    else mbar_arrive(smem_u32(done));
+  }
+  __syncwarp();
+
+  // ----------------------------------------------------------- epilogue
+  const bool done_ok = mbar_wait(smem_u32(done), 0u, err);
+  __syncwarp();
+  tc_fence_after();
+  const int m = m0 + warp * 32 + lane;  // this thread's tile row
+  const bool mvalid = m < g.M;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  // warp-uniform: tcgen05.ld is executed by all lanes of a warp or none
+  const bool acc_valid = __all_sync(0xffffffffu, nkt > 0 && done_ok);
+  float rowsum = 0.0f;
+  const bool want_col = g.col_part && ((op == kOpOut && g.coef) || op == kOpGA);
+  const float cm = (op == kOpOut && g.coef && mvalid) ? g.coef[m] : 0.0f;
+
+  for (int c0 = 0; c0 < BN; c0 += 16) {
+    float v[16];
+    if (acc_valid) {
+      tmem_ld16(trow + (uint32_t)c0, v);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+    }
+    float cs[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int nn = n0 + c0 + q;
+      const bool in = mvalid && nn < g.N;
+      float colv = 0.0f;
+      if (op == kOpHidden) {
+        if (in) {
+          float x = v[q] + g.bias[nn];
+          x = g.act == VQMC_ACT_RELU ? fmaxf(x, 0.0f) : sigmoidf_(x);
+          const bf16 t = __float2bfloat16_rn(x);
+          g.out[(size_t)m * g.ldo + nn] = t;
+          g.out_t[(size_t)nn * g.ldt + m] = t;
+        }
+      } else if (op == kOpOut) {
+        if (in) {
+          const float z = v[q] + g.bias[nn];
+          const float s = g.S8[(size_t)m * g.lds8 + nn] > 0 ? 1.0f : -1.0f;
+          rowsum += log_sigmoidf_(s * z);
+          if (g.coef) {
+            const float d = cm * s * sigmoidf_(-s * z);
+            const bf16 t = __float2bfloat16_rn(d);
+            g.out[(size_t)m * g.ldo + nn] = t;
+            g.out_t[(size_t)nn * g.ldt + m] = t;
+            colv = d;
+          }
+        }
+      } else if (op == kOpGA) {
+        if (in) {
+          const float hv = __bfloat162float(g.aux[(size_t)m * g.ldaux + nn]);
+          const float da = g.act == VQMC_ACT_RELU ? (hv > 0.0f ? 1.0f : 0.0f) : hv * (1.0f - hv);
+          const float x = v[q] * da;
+          g.out_t[(size_t)nn * g.ldt + m] = __float2bfloat16_rn(x);
+          colv = x;
+        }
+      } else if (op == kOpDV || op == kOpDW) {
+        if (in) g.gout[(size_t)m * g.ldg + nn] = gemm_out_kept(op, m, nn, g.n, g.h) ? v[q] : 0.0f;
+      } else if (op == kOpEloc) {
+        if (in) {
+          const float s = g.S8[(size_t)m * g.lds8 + nn] > 0 ? 0.5f : -0.5f;
+          rowsum = fmaf(s, v[q], rowsum);
+        }
+      }
+      cs[q] = colv;
+    }
+    if (want_col) {
+      const float w = colsum16(cs, lane);
+      if ((lane & 1) == 0) colbuf[warp * BN + c0 + colsum16_col(lane)] = w;
+    }
+  }
+  if (g.row_part && (op == kOpOut || op == kOpEloc) && mvalid) g.row_part[(size_t)blockIdx.x * g.ldr + m] = rowsum;
+  tc_fence_before();
+  __syncthreads();
+  if (want_col && tid < BN && n0 + tid < g.N) {
+    const float v = colbuf[tid] + colbuf[BN + tid] + colbuf[2 * BN + tid] + colbuf[3 * BN + tid];
+    g.col_part[(size_t)blockIdx.y * g.ldc + n0 + tid] = v;
+  }
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ------------------------------------------------------------ host side
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_once;
+bool g_have_tc = false;
+
+void init_once() {
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess && fn) {
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  int dev = 0, major = 0, minor = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  g_have_tc = g_encode != nullptr && major == 10 && minor == 3;
+  if (g_have_tc &&
+      cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
+    g_have_tc = false;
+}
+
+// rows x cols (cols contiguous, leading dimension ld elements) BF16 matrix,
+// boxes of 64 columns x 128 rows, 128-byte swizzle, zero fill outside.
+bool encode(CUtensorMap* map, const void* ptr, int rows, int cols, int ld) {
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool gemm_tc_available() {
+  std::call_once(g_once, init_once);
+  return g_have_tc;
+}
+
+cudaError_t launch_gemm_tc_bf16(const GemmArgs<bf16>& a, cudaStream_t st) {
+  if (!gemm_tc_available()) return cudaErrorNotSupported;
+  if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+  // operand row strides must be multiples of 16 bytes, K at least one element
+  if ((a.lda * 2) % 16 || (a.ldb * 2) % 16 || a.K <= 0) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb, mb2;
+  if (!encode(&ma, a.A, a.M, a.K, a.lda) || !encode(&mb, a.Bm, a.N, a.K, a.ldb)) return cudaErrorInvalidValue;
+  if (a.Bm2) {
+    if (!encode(&mb2, a.Bm2, a.N, a.K, a.ldb)) return cudaErrorInvalidValue;
+  } else {
+    mb2 = mb;
+  }
+  dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM);
+  gemm_tc_kernel<<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, a.Bm2 ? 1 : 0);
+  return cudaGetLastError();
+}
 
 }  // namespace vqmc

@@ -70,6 +70,7 @@ GemmArgs<T> make_args(const vqmc_ctx* c, GemmOp op, int B, const int8_t* d_s, co
   a.act = c->act;
   a.ldr = c->row_part_ld;
   a.ldc = c->col_part_ld;
+  a.err = c->err;
   const int n = c->n, h = c->h;
   switch (op) {
     case kOpHidden:
@@ -132,8 +133,8 @@ cudaError_t launch_gemm(const vqmc_ctx* c, GemmOp op, int B, const int8_t* d_s, 
   if (c->prec == VQMC_PREC_BF16) {
     GemmArgs<bf16> a = make_args<bf16>(c, op, B, d_s, coef, grad);
     if (op == kOpEloc) a.Bm = (const bf16*)c->J_hi, a.Bm2 = (const bf16*)c->J_lo;
-    if (gemm_tc_available()) return launch_gemm_tc_bf16(a, st);
-    return launch_gemm_simt_bf16(a, st);
+    // BF16 GEMMs run on the tcgen05 tensor cores only (sm_103a); no fallback
+    return launch_gemm_tc_bf16(a, st);
   }
   GemmArgs<float> a = make_args<float>(c, op, B, d_s, coef, grad);
   if (op == kOpEloc) a.Bm = c->J;
