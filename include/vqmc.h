@@ -253,6 +253,28 @@ enum {
 vqmc_status vqmc_timing_enable(vqmc_ctx* ctx, int enable);
 vqmc_status vqmc_timing_read(vqmc_ctx* ctx, double* ms_out, int64_t* steps_out, int64_t* launches_out);
 
+/* Allocation-free variant of vqmc_logprob.  The paper has no counterpart to
+ * this entry point: it exists for callers that cannot allocate device memory
+ * at call time -- code whose device memory is owned by another framework's
+ * pool, serving paths with a fixed memory budget, or code that must not let
+ * a cudaMalloc/cudaFree synchronise the device.  It computes the same log pi
+ * as vqmc_logprob (same kernels, same arithmetic) but takes its scratch (the
+ * spin operand, the hidden activations and the row partial sums) from one
+ * static device array of 64 MiB owned by the library instead of the context.
+ * It calls no allocating routine.  Limits and caveats:
+ *   - the scratch a call needs grows with B, n and h; a call that would need
+ *     more than 64 MiB returns VQMC_ERR_UNSUPPORTED with the byte count
+ *     (at n = 10,000, h = 2,000 that is about B <= 2,300 in BF16);
+ *   - every GPU that loads the library's module holds the 64 MiB until the
+ *     process exits;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - all calls share the array, so calls that overlap on the GPU (on other
+ *     streams or from other threads) race and must be serialised by the
+ *     caller.
+ * Arguments and errors as vqmc_logprob. */
+vqmc_status vqmc_logprob_noalloc(vqmc_ctx* ctx, int32_t B, const int8_t* d_s, float* d_logp, vqmc_stream stream);
+
 /* Thread-local description of the last error. */
 const char* vqmc_last_error(void);
 

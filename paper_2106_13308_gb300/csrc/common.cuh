@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 #include "vqmc.h"
 
@@ -147,6 +148,12 @@ enum GemmOp {
 };
 cudaError_t launch_gemm(const vqmc_ctx* c, GemmOp op, int B, const int8_t* d_s, const float* coef,
                         float* grad, cudaStream_t st);
+
+// ---- vqmc_api.cu: sets the thread-local message of vqmc_last_error
+vqmc_status set_last_error(vqmc_status s, const std::string& msg);
+
+// ---- noalloc.cu: scratch bytes vqmc_logprob_noalloc needs for B samples
+size_t noalloc_scratch_bytes(const vqmc_ctx* c, int B);
 
 // ---- adam.cu
 cudaError_t launch_mask_params(vqmc_ctx* c, cudaStream_t st);

@@ -128,6 +128,8 @@ GemmArgs<T> make_args(const vqmc_ctx* c, GemmOp op, int B, const int8_t* d_s, co
 
 namespace vqmc {
 
+vqmc_status set_last_error(vqmc_status s, const std::string& msg) { return fail(s, msg); }
+
 cudaError_t launch_gemm(const vqmc_ctx* c, GemmOp op, int B, const int8_t* d_s, const float* coef, float* grad,
                         cudaStream_t st) {
   if (c->prec == VQMC_PREC_BF16) {

@@ -34,7 +34,7 @@ EXPORTS = [
     "vqmc_params_device", "vqmc_params_updated", "vqmc_uniforms", "vqmc_sample", "vqmc_local_energy",
     "vqmc_logprob", "vqmc_logprob_backward", "vqmc_energy_stats", "vqmc_grad", "vqmc_adam", "vqmc_step",
     "vqmc_last_batch", "vqmc_iteration", "vqmc_check", "vqmc_save", "vqmc_load", "vqmc_timing_enable",
-    "vqmc_timing_read", "vqmc_last_error",
+    "vqmc_timing_read", "vqmc_logprob_noalloc", "vqmc_last_error",
 ]
 PARTS = ["sample", "energy", "stats", "grad", "adam"]
 
@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH):
         "vqmc_load": (st, [P, ctypes.c_char_p]),
         "vqmc_timing_enable": (st, [P, ctypes.c_int]),
         "vqmc_timing_read": (st, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "vqmc_logprob_noalloc": (st, [P, I32, P, P, P]),
         "vqmc_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -180,6 +181,10 @@ def vqmc_local_energy(ctx, B: int, s: torch.Tensor, e: torch.Tensor, stream=None
 
 def vqmc_logprob(ctx, B: int, s: torch.Tensor, logp: torch.Tensor, stream=None):
     _check(load_library().vqmc_logprob(ctx, B, _ptr(s), _ptr(logp), _stream(stream)))
+
+
+def vqmc_logprob_noalloc(ctx, B: int, s: torch.Tensor, logp: torch.Tensor, stream=None):
+    _check(load_library().vqmc_logprob_noalloc(ctx, B, _ptr(s), _ptr(logp), _stream(stream)))
 
 
 def vqmc_logprob_backward(ctx, B: int, s, gout, grad, stream=None):
