@@ -43,6 +43,21 @@ def _dist_env():
     return rank, world, local
 
 
+def _recorded_traffic(kernel, source, workload):
+    """DRAM bytes per launch from the ncu record in profiles/, or None when the
+    kernel's source changed since the counters were taken."""
+    import hashlib
+    try:
+        sha = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()[:12]
+        for line in open(os.path.join(ROOT, "profiles", "roofline_traffic.txt")):
+            f = line.split()
+            if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[3] == workload:
+                return int(f[2]) if f[1] == sha else None
+    except OSError:
+        return None
+    return None
+
+
 def _workload(name):
     from paper_2106_13308_gb300 import inputs
     cfg = inputs.config(name)
@@ -310,8 +325,9 @@ def main():
     sample_ms = parts["sample"] / max(steps, 1)
     flops = 2.0 * cfg["h"] * cfg["n"] * B
     achieved = flops / (sample_ms / 1000.0) / 1e12
+    traffic = _recorded_traffic("sampler_kernel", "paper_2106_13308_gb300/csrc/sampler.cu", f"{args.config}_bf16")
     roofline = {"bound": "alu", "kernel": "sampler_kernel (FP32 FMA pipe)", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {peak_mhz:.0f} MHz (fallback: no "
                                "measured FP32 peak)",
                 "algorithmic": f"2*h*n*B = {flops:.3e} flop per launch (h*n FMA per sample)"}
