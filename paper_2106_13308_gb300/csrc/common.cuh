@@ -123,7 +123,7 @@ namespace vqmc {
 // ---- sampler.cu
 cudaError_t launch_uniforms(int B, int n, uint64_t seed, uint64_t iteration, float* d_u, cudaStream_t st);
 cudaError_t launch_sampler(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,
-                           float* d_logp, void* Sx, void* St, cudaStream_t st);
+                           float* d_logp, cudaStream_t st);
 
 // ---- eloc.cu
 cudaError_t launch_eloc_sparse(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st);

@@ -1,0 +1,6 @@
+// Sampler instantiations for BF16 weights.
+#include "sampler_impl.cuh"
+
+namespace vqmc {
+template cudaError_t launch_sampler_wt<bf16>(const SamplerArgs& a, cudaStream_t st);
+}  // namespace vqmc

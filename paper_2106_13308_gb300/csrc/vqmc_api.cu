@@ -359,7 +359,7 @@ vqmc_status vqmc_sample(vqmc_ctx* c, int32_t B, const float* d_u, uint64_t itera
   vqmc_status s = check_B(c, B);
   if (s != VQMC_OK) return s;
   if (B > 0 && !d_s) return fail(VQMC_ERR_INVALID_ARG, "null output");
-  VQ_CUDA(launch_sampler(c, B, d_u, iteration, d_s, d_logp, nullptr, nullptr, S(stream)));
+  VQ_CUDA(launch_sampler(c, B, d_u, iteration, d_s, d_logp, S(stream)));
   return VQMC_OK;
 }
 
@@ -462,8 +462,9 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
     if (ev) cudaEventRecord(ev[part], st);
   };
   mark(0);
-  // (a) exact samples; the sampler also writes the GEMM operand layouts
-  VQ_CUDA(launch_sampler(c, B, nullptr, c->iter, c->S, nullptr, c->Sx, c->St, st));
+  // (a) exact samples, then their GEMM operand layouts
+  VQ_CUDA(launch_sampler(c, B, nullptr, c->iter, c->S, nullptr, st));
+  VQ_CUDA(launch_spins_to_operands(c, B, c->S, c->Sx, c->St, st));
   mark(1);
   // (c) local energies
   if (c->ham == VQMC_HAM_DENSE_F32) {
@@ -487,8 +488,9 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
   if (h_out) VQ_CUDA(cudaMemcpyAsync(h_out, c->step_stats, sizeof(vqmc_step_stats), cudaMemcpyDeviceToHost, st));
   if (timed) {
     c->timed_steps += 1;
-    // sampler, energy (2 for dense), stats, 7 gradient kernels, Adam + 3 refresh kernels, stats copy
-    c->launches += 1 + (c->ham == VQMC_HAM_DENSE_F32 ? 2 : 1) + 1 + 7 + 4 + 1;
+    // sampler + operand layouts, energy (2 for dense), stats, 7 gradient kernels, Adam + 3 refresh
+    // kernels, stats copy
+    c->launches += 2 + (c->ham == VQMC_HAM_DENSE_F32 ? 2 : 1) + 1 + 7 + 4 + 1;
   }
   c->iter += 1;
   return VQMC_OK;
