@@ -97,17 +97,27 @@ __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
   return d;
 }
 
-// weights of units (2q, 2q+1) of a staged row as an FP32 pair
+// Weights of units (2q, 2q+1) of a staged row: raw (as stored) and as an
+// FP32 pair.  BF16 widens exactly by a shift.
 template <typename T>
-__device__ __forceinline__ uint64_t ld_pair(const T* row, int q);
+struct Pair;
 template <>
-__device__ __forceinline__ uint64_t ld_pair<bf16>(const bf16* row, int q) {
-  const uint32_t x = reinterpret_cast<const uint32_t*>(row)[q];
-  return pack2(__uint_as_float(x << 16), __uint_as_float(x & 0xffff0000u));
-}
+struct Pair<bf16> {
+  using raw = uint32_t;
+  static __device__ __forceinline__ raw ld(const bf16* row, int q) { return reinterpret_cast<const uint32_t*>(row)[q]; }
+  static __device__ __forceinline__ uint64_t f32(raw x) {
+    return pack2(__uint_as_float(x << 16), __uint_as_float(x & 0xffff0000u));
+  }
+};
 template <>
-__device__ __forceinline__ uint64_t ld_pair<float>(const float* row, int q) {
-  return reinterpret_cast<const uint64_t*>(row)[q];
+struct Pair<float> {
+  using raw = uint64_t;
+  static __device__ __forceinline__ raw ld(const float* row, int q) { return reinterpret_cast<const uint64_t*>(row)[q]; }
+  static __device__ __forceinline__ uint64_t f32(raw x) { return x; }
+};
+template <typename T>
+__device__ __forceinline__ uint64_t ld_pair(const T* row, int q) {
+  return Pair<T>::f32(Pair<T>::ld(row, q));
 }
 
 
@@ -140,11 +150,12 @@ struct Sampler {
 
   // Mixed slot: the lane's two units may be in different roles.  Weights of
   // units that must not take part are zeroed, so the pair still runs as f32x2.
-  static __device__ __forceinline__ void mixed(State& st, const WT* wrow, const WT* vrow, int r, int q, int i,
-                                               int m0, int m1, int g_act) {
-    if (i >= 2 && (m0 >= i - 1 || m1 >= i - 1)) {
+  // (At i = 1 the spins are still zero, so the update adds nothing.)
+  static __device__ __forceinline__ void mixed(State& st, uint64_t wpair, uint64_t vpair, int r, int i, int m0,
+                                               int m1, int g_act) {
+    if (m0 >= i - 1 || m1 >= i - 1) {
       float w0, w1;
-      unpack2(ld_pair(wrow, q), w0, w1);
+      unpack2(wpair, w0, w1);
       const uint64_t w = pack2(m0 >= i - 1 ? w0 : 0.0f, m1 >= i - 1 ? w1 : 0.0f);
 #pragma unroll
       for (int s = 0; s < SL; ++s) st.a[r][s] = fma2(w, st.sg[s], st.a[r][s]);
@@ -161,7 +172,7 @@ struct Sampler {
     }
     if (m0 <= i - 1) {
       float v0, v1;
-      unpack2(ld_pair(vrow, q), v0, v1);
+      unpack2(vpair, v0, v1);
       const uint64_t v = pack2(v0, m1 <= i - 1 ? v1 : 0.0f);
 #pragma unroll
       for (int s = 0; s < SL; ++s) st.acc[s] = fma2(v, st.a[r][s], st.acc[s]);
@@ -169,26 +180,35 @@ struct Sampler {
   }
 
   // Slots r < ND: every unit complete -> dot.  MIX: slot ND is mixed.
-  // Remaining slots: every unit still accumulating -> update.
+  // Remaining slots: every unit still accumulating -> update.  wp[r] holds
+  // the W2 pair of a dot slot and the W1 pair of the others; wq the W2 pair
+  // of the mixed slot.
+  using PR = typename Pair<WT>::raw;
   template <int ND, bool MIX>
-  static __device__ __forceinline__ void body(State& st, const WT* __restrict__ wrow, const WT* __restrict__ vrow,
-                                              int lq, int i, int m0, int m1, int g_act) {
+  static __device__ __forceinline__ void body(State& st, const PR (&wp)[U2], PR wq, int i, int m0, int m1,
+                                              int g_act) {
 #pragma unroll
     for (int r = 0; r < ND && r < U2; ++r) {
-      const uint64_t w = ld_pair(vrow, lq + r * GL);
+      const uint64_t w = Pair<WT>::f32(wp[r]);
 #pragma unroll
       for (int s = 0; s < SL; ++s) st.acc[s] = fma2(w, st.a[r][s], st.acc[s]);
     }
     constexpr int FIRST_UPD = MIX ? ND + 1 : ND;
-    if constexpr (MIX && ND < U2) mixed(st, wrow, vrow, ND, lq + ND * GL, i, m0, m1, g_act);
-    if (i >= 2) {
+    if constexpr (MIX && ND < U2) mixed(st, Pair<WT>::f32(wp[ND]), Pair<WT>::f32(wq), ND, i, m0, m1, g_act);
 #pragma unroll
-      for (int r = FIRST_UPD; r < U2; ++r) {
-        const uint64_t w = ld_pair(wrow, lq + r * GL);
+    for (int r = FIRST_UPD; r < U2; ++r) {
+      const uint64_t w = Pair<WT>::f32(wp[r]);
 #pragma unroll
-        for (int s = 0; s < SL; ++s) st.a[r][s] = fma2(w, st.sg[s], st.a[r][s]);
-      }
+      for (int s = 0; s < SL; ++s) st.a[r][s] = fma2(w, st.sg[s], st.a[r][s]);
     }
+  }
+
+  // the pairs body<ND, MIX> reads, from the staged rows of its step
+  template <int ND, bool MIX>
+  static __device__ __forceinline__ void load(PR (&wp)[U2], PR& wq, const WT* wrow, const WT* vrow, int lq) {
+#pragma unroll
+    for (int r = 0; r < U2; ++r) wp[r] = Pair<WT>::ld(r < ND ? vrow : wrow, lq + r * GL);
+    if constexpr (MIX && ND < U2) wq = Pair<WT>::ld(vrow, lq + ND * GL);
   }
 
   // every slot treated as mixed (small n or h >> n)
@@ -197,7 +217,7 @@ struct Sampler {
 #pragma unroll
     for (int r = 0; r < U2; ++r) {
       const int q = lq + r * GL;
-      mixed(st, wrow, vrow, r, q, i, deg(2 * q, n, h), deg(2 * q + 1, n, h), g_act);
+      mixed(st, ld_pair(wrow, q), ld_pair(vrow, q), r, i, deg(2 * q, n, h), deg(2 * q + 1, n, h), g_act);
     }
   }
 
@@ -268,10 +288,11 @@ struct Run {
   float cw, cnx;        // b2 of this / the next 32 steps, lane l holds step win+l
   float lp;
   uint32_t bits;        // drawn spins of the current 32-step window (writer lanes)
-  int cs;               // ring stage of the current block
+  int cs;               // ring stage holding the current step's rows
   uint32_t cpar;        // its fill parity
   int i;                // next step (1-based)
   int m0, m1;           // degrees of this lane's units in the mixed slot
+  typename K::PR wp[U2], wq;  // this step's weight pairs, loaded one step ahead
 
   __device__ __forceinline__ Run(const SamplerArgs& a) : g(a) {}
 
@@ -283,6 +304,19 @@ struct Run {
     mbar_expect_tx(bar, 2 * block_bytes);
     bulk_g2s(smem_u32(dst), gwt + (size_t)q * SPS * hp, block_bytes, bar);
     bulk_g2s(smem_u32(dst + SPS * hp), gv + (size_t)q * SPS * hp, block_bytes, bar);
+  }
+
+  __device__ __forceinline__ const WT* wrow_of(int t) const { return stages + (size_t)cs * stage_elems + (t & (SPS - 1)) * hp; }
+
+  // bounded wait for the current stage's copies
+  __device__ __forceinline__ void wait_stage() {
+    const uint32_t fb = smem_u32(&full[cs]);
+    bool got = !ok;
+    for (long long it = 0; it < kSpinLimit && !got; ++it) got = mbar_try_wait(fb, cpar);
+    if (!got) {
+      atomicOr(g.err, kErrTimeout);
+      ok = false;  // run on without waiting: every warp still reaches every named barrier
+    }
   }
 
   __device__ __forceinline__ void load_u(int win, float (&dst)[4]) {
@@ -312,11 +346,13 @@ struct Run {
     }
   }
 
-  // one step: windows, ring, body, reduction, draw
+  // One step.  The weights of step i were loaded during step i-1; this step
+  // loads those of step i+1 right after its own FMAs, so the shared-memory
+  // latency hides behind the reduction and the draw.
   template <int ND, bool MIX, bool GEN>
   __device__ __forceinline__ void step() {
     const int t = i - 1;
-    if (t % UWIN == 0) {
+    if ((t & (UWIN - 1)) == 0) {
       if (g.u) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) uw[e] = logit(unx[e]);
@@ -332,25 +368,17 @@ struct Run {
       cw = cnx;
       cnx = (t + 32 + lane < n) ? __ldg(g.b2 + t + 32 + lane) : 0.0f;
     }
-    const int ro = t % SPS;
-    if (ro == 0 && t > 0 && ++cs == nst) cs = 0, cpar ^= 1u;
-    if (ro == 0) {
-      const uint32_t fb = smem_u32(&full[cs]);
-      bool got = !ok;
-      for (long long it = 0; it < kSpinLimit && !got; ++it) got = mbar_try_wait(fb, cpar);
-      if (!got) {
-        atomicOr(g.err, kErrTimeout);
-        ok = false;  // run on without waiting: every warp still reaches every named barrier
-      }
-    }
-    const WT* wrow = stages + (size_t)cs * stage_elems + ro * hp;
-    const WT* vrow = wrow + SPS * hp;
+    const int ro = t & (SPS - 1);
 #pragma unroll
     for (int q = 0; q < SL; ++q) st.acc[q] = pack2(0.0f, 0.0f);
-    if constexpr (GEN) K::body_general(st, wrow, vrow, L, i, n, h, g.act);
-    else K::template body<ND, MIX>(st, wrow, vrow, L, i, m0, m1, g.act);
+    if constexpr (GEN) {
+      const WT* wrow = wrow_of(t);
+      K::body_general(st, wrow, wrow + SPS * hp, L, i, n, h, g.act);
+    } else {
+      K::template body<ND, MIX>(st, wp, wq, i, m0, m1, g.act);
+    }
     if (ro == SPS - 1 || i == n) {
-      // done with the block's rows; the last warp to release refills the stage
+      // done with the stage; the last warp to release it refills it
       __syncwarp();
       if (lane == 0) {
         __threadfence_block();
@@ -360,6 +388,17 @@ struct Run {
           const int q = t / SPS + nst;
           if (q < nblocks) issue(q);
         }
+      }
+    }
+    if (i < n) {
+      if (ro == SPS - 1) {
+        if (++cs == nst) cs = 0, cpar ^= 1u;
+        wait_stage();
+      }
+      if constexpr (!GEN) {
+        // next step's pairs, with this phase's roles (a new phase reloads)
+        const WT* wrow = wrow_of(t + 1);
+        K::template load<ND, MIX>(wp, wq, wrow, wrow + SPS * hp, L);
       }
     }
     // z_i: lanes -> warp (shuffles) -> group (shared memory + named barrier)
@@ -374,36 +413,37 @@ struct Run {
     const float ws = K::reduce_scatter(v, lane, qs);
     float* rb = gred + (size_t)(t & 1) * NGRP * GW * SL;
     if ((lane & (32 / SL - 1)) == 0) rb[wg * SL + qs] = ws;
-    if constexpr (GW > 1) asm volatile("barrier.sync %0, %1;" ::"r"(1 + grp), "r"(GW * 32) : "memory");
-    else __syncwarp();
-    float z = __shfl_sync(0xffffffffu, cw, t & 31);
-    if (lane < SL) {
-#pragma unroll
-      for (int w = 0; w < GW; ++w) z += rb[w * SL + lane];
-    }
-    const int src = ((t % UWIN) >> 2) * SL + (lane < SL ? lane : 0);
     const int e = t & 3;
     const float lsel = e == 0 ? uw[0] : e == 1 ? uw[1] : e == 2 ? uw[2] : uw[3];
-    const bool up = z > __shfl_sync(0xffffffffu, lsel, src);  // u < sigma(z)
+    const float lg = __shfl_sync(0xffffffffu, lsel, ((t & (UWIN - 1)) >> 2) * SL + (lane & (SL - 1)));
+    float z = __shfl_sync(0xffffffffu, cw, t & 31);
+    if constexpr (GW > 1) asm volatile("barrier.sync %0, %1;" ::"r"(1 + grp), "r"(GW * 32) : "memory");
+    else __syncwarp();
+    // lanes >= SL compute a copy of lane (lane % SL)'s value; only bits < SL are used
+#pragma unroll
+    for (int w = 0; w < GW; ++w) z += rb[w * SL + (lane & (SL - 1))];
+    const bool up = z > lg;  // u < sigma(z)
     const uint32_t mask = __ballot_sync(0xffffffffu, up);
 #pragma unroll
     for (int q = 0; q < SL; ++q) {
       const float sv = ((mask >> q) & 1u) ? 1.0f : -1.0f;
       st.sg[q] = pack2(sv, sv);
     }
-    if (writer) {
-      if (g.logp) lp += log_sigmoid(up ? z : -z);
-      bits |= (up ? 1u : 0u) << (t & 31);
-      if ((t & 31) == 31 || i == n) {
-        flush(t);
-        bits = 0;
-      }
+    bits |= (up ? 1u : 0u) << (t & 31);
+    if (g.logp && writer) lp += log_sigmoid(up ? z : -z);
+    if ((t & 31) == 31 || i == n) {
+      if (writer) flush(t);
+      bits = 0;
     }
     ++i;
   }
 
   template <int ND, bool MIX, bool GEN>
   __device__ __forceinline__ void steps(int i_end) {
+    if constexpr (!GEN) {
+      const WT* wrow = wrow_of(i - 1);
+      K::template load<ND, MIX>(wp, wq, wrow, wrow + SPS * hp, L);
+    }
     while (i < i_end) step<ND, MIX, GEN>();
   }
 
@@ -499,6 +539,7 @@ __global__ void __launch_bounds__(GW * NGRP * 32, 1) sampler_kernel(const Sample
   R.bits = 0;
   R.cs = 0, R.cpar = 0;
   R.i = 1;
+  R.wait_stage();
 
   // warp-uniform slot bookkeeping: nd = #slots complete before step i, nt =
   // #slots with at least one unit complete at step i; thresholds are the
