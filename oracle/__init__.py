@@ -34,6 +34,8 @@ _lock = threading.Lock()
 _lib = None
 
 RELU, SIGMOID = 0, 1
+# OR into an activation code: hidden activations rounded to bfloat16 (the BF16 model)
+HIDDEN_BF16 = 2
 
 
 def build(force: bool = False) -> str:
@@ -56,6 +58,8 @@ def _load():
             P = ctypes.c_void_p
             I = ctypes.c_int
             D = ctypes.c_double
+            lib.vo_round_bf16.restype = D
+            lib.vo_round_bf16.argtypes = [D]
             lib.vo_degree.restype = ctypes.c_long
             lib.vo_degree.argtypes = [ctypes.c_long] * 3
             lib.vo_num_threads.restype = I
@@ -93,6 +97,13 @@ def _i8(a):
 
 def _i32(a):
     return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def round_bf16(x) -> np.ndarray:
+    """Each value rounded to the nearest bfloat16 (ties to even), as float64."""
+    lib = _load()
+    flat = np.asarray(x, dtype=np.float64).ravel()
+    return np.array([lib.vo_round_bf16(float(v)) for v in flat], dtype=np.float64).reshape(np.shape(x))
 
 
 def num_threads() -> int:

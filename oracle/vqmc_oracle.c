@@ -16,6 +16,12 @@
  *   The paper's hidden activation is the rectifier; the logistic sigmoid is
  *   the alternative activation selected with act = 1.
  *
+ * Reduced precision (Sec. 4 runs the network in mixed precision; the BF16
+ * model of this library is read as: weights rounded to bfloat16, each hidden
+ * activation g1_k rounded to bfloat16 before the output layer, everything
+ * else exact).  act | VO_HIDDEN_BF16 selects that rounding of g1; the weights
+ * are rounded by the caller.
+ *
  * Masks (the paper only asks for "appropriate binary masks", Sec. 2.3; the
  * reading used here is the standard MADE degree rule with sorted degrees):
  *   hidden unit k (0-based) has degree m(k) = 1 + floor(k (n-1) / h);
@@ -107,11 +113,30 @@ static double log_sigmoid(double t) {
   return t - log1p(exp(t));
 }
 
-static double act_f(int act, double a) { return act == 0 ? (a > 0 ? a : 0.0) : sigmoid(a); }
+#define VO_HIDDEN_BF16 2
 
-/* derivative of the activation at pre-activation a (ReLU'(0) = 0). */
+/* x rounded to the nearest bfloat16 value (IEEE binary32 exponent range, 8
+ * significant bits, ties to even; subnormals keep the fixed spacing 2^-133).
+ * rint rounds ties to even in the default rounding mode. */
+double vo_round_bf16(double x) {
+  if (x == 0.0 || isnan(x) || isinf(x)) return x;
+  int e;
+  frexp(x, &e);          /* |x| = f 2^e, f in [0.5, 1) */
+  int q = e - 8;         /* spacing of 8-bit significands at this binade */
+  if (q < -133) q = -133;
+  return ldexp(rint(ldexp(x, -q)), q);
+}
+
+static double act_f(int act, double a) {
+  double g = (act & 1) == 0 ? (a > 0 ? a : 0.0) : sigmoid(a);
+  return (act & VO_HIDDEN_BF16) ? vo_round_bf16(g) : g;
+}
+
+/* derivative of the activation at pre-activation a (ReLU'(0) = 0); the
+ * bfloat16 rounding of g1 is not differentiated (it is the identity up to
+ * rounding). */
 static double act_d(int act, double a) {
-  if (act == 0) return a > 0 ? 1.0 : 0.0;
+  if ((act & 1) == 0) return a > 0 ? 1.0 : 0.0;
   double g = sigmoid(a);
   return g * (1.0 - g);
 }

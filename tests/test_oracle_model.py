@@ -67,7 +67,11 @@ def test_degrees_sorted_and_in_range():
         assert m[0] == 1 and np.all(np.diff(m) >= 0) and m.max() <= max(n - 1, 1)
 
 
-@pytest.mark.parametrize("act", [oracle.RELU, oracle.SIGMOID])
+BF16_RELU = oracle.RELU | oracle.HIDDEN_BF16
+BF16_SIGMOID = oracle.SIGMOID | oracle.HIDDEN_BF16
+
+
+@pytest.mark.parametrize("act", [oracle.RELU, oracle.SIGMOID, BF16_RELU, BF16_SIGMOID])
 def test_autoregressive_property(act):
     """z_i depends only on s_<i: changing s_i..s_n leaves z_i unchanged."""
     n, h = 13, 29
@@ -85,7 +89,7 @@ def test_autoregressive_property(act):
     # with h >= n - 1 every degree 1..n-1 is used, so z_i depends on s_{i-1}
     # for every i >= 2 (M1 uses m(k) >= j, M2 uses i > m(k): maximal
     # connectivity).  Checked with the sigmoid, which has no dead units.
-    if act != oracle.SIGMOID:
+    if act & 1 != oracle.SIGMOID:
         return
     for i in range(1, n):
         t = s.copy()
@@ -94,13 +98,66 @@ def test_autoregressive_property(act):
         assert z3[i] != z[i], i
 
 
-@pytest.mark.parametrize("n,h,act", [(12, 20, oracle.RELU), (12, 20, oracle.SIGMOID), (20, 40, oracle.SIGMOID)])
+@pytest.mark.parametrize("n,h,act", [(12, 20, oracle.RELU), (12, 20, oracle.SIGMOID), (20, 40, oracle.SIGMOID),
+                                     (12, 20, BF16_RELU), (14, 9, BF16_SIGMOID)])
 def test_normalisation_by_enumeration(n, h, act):
     """sum_s pi(s) = 1 (autoregressive normalisation, Sec. 2.3)."""
     P = _params(n, h, 5)
     inst = _small_instance(n, 6)
     out = oracle.enumerate_exact(P, inst, act)
     assert abs(out[0] - 1.0) < 1e-12
+
+
+# ------------------------------------------------ bfloat16 hidden layer
+
+def test_round_bf16_matches_library_conversion():
+    """vo_round_bf16 on binary32 inputs equals the library's float -> bfloat16
+    conversion (round to nearest, ties to even): random magnitudes, exact
+    halfway cases with even and odd kept significands, subnormals, signs."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(31)
+    x = (rng.standard_normal(3000) * np.exp2(rng.integers(-40, 40, 3000))).astype(np.float32)
+    bits = rng.integers(0, 1 << 16, 400, dtype=np.uint32) << 16
+    halfway = ((bits | 0x8000) & 0x7F7FFFFF).view(np.float32)  # exactly between two bf16 values
+    sub = (rng.integers(1, 1 << 23, 200, dtype=np.uint32)).view(np.float32)  # binary32 subnormals
+    vals = np.concatenate([x, -x[:500], halfway, -halfway[:100], sub, np.float32([0.0, 1.0, -2.5, 3.0e38])])
+    ref = torch.from_numpy(vals).to(torch.bfloat16).to(torch.float64).numpy()
+    got = oracle.round_bf16(vals.astype(np.float64))
+    assert np.array_equal(got, ref)
+
+
+def test_hidden_bf16_is_identity_on_representable_activations():
+    """With integer weights and biases every ReLU activation is a small
+    integer, exactly representable in bfloat16, so the BF16 hidden layer
+    gives the same logits as the exact one."""
+    n, h = 9, 14
+    rng = np.random.default_rng(33)
+    th = oracle.made_to_theta(rng.integers(-3, 4, (h, n)).astype(np.float64), rng.integers(-2, 3, h).astype(np.float64),
+                              rng.integers(-3, 4, (n, h)).astype(np.float64), rng.integers(-2, 3, n).astype(np.float64))
+    P = oracle.theta_to_made(th, n, h)
+    S = inputs.spins(16, n, 34)
+    assert np.array_equal(oracle.logits(P, S, oracle.RELU), oracle.logits(P, S, BF16_RELU))
+
+
+@pytest.mark.parametrize("act", [oracle.RELU, oracle.SIGMOID])
+def test_hidden_bf16_logit_shift_within_rounding_bound(act):
+    """Rounding each g1_k to 8 significant bits moves z_i by at most
+    sum_k |W2_ik| |g1_k| 2^-8 (relative rounding error of bfloat16 <= 2^-9,
+    doubled for slack), and it does move some logits."""
+    n, h = 30, 45
+    P = _params(n, h, 35)
+    S = inputs.spins(8, n, 36)
+    W1, b1, W2, b2 = P
+    Z = oracle.logits(P, S, act)
+    Zq = oracle.logits(P, S, act | oracle.HIDDEN_BF16)
+    m = oracle.degrees(n, h)
+    for b in range(S.shape[0]):
+        a, _ = oracle.forward(P, S[b], act)
+        g = np.maximum(a, 0) if act == oracle.RELU else 1 / (1 + np.exp(-a))
+        M2 = (np.arange(1, n + 1)[:, None] > m[None, :])
+        bound = (np.abs(W2) * M2) @ np.abs(g) * 2.0 ** -8
+        assert np.all(np.abs(Zq[b] - Z[b]) <= bound + 1e-15)
+    assert np.any(Zq != Z)
 
 
 def test_independent_spins_closed_forms():
@@ -204,7 +261,8 @@ def test_batch_gradient_finite_differences():
 
 # --------------------------------------------------------------- sampling
 
-@pytest.mark.parametrize("n,h,act", [(40, 60, oracle.RELU), (40, 17, oracle.SIGMOID), (25, 25, oracle.RELU)])
+@pytest.mark.parametrize("n,h,act", [(40, 60, oracle.RELU), (40, 17, oracle.SIGMOID), (25, 25, oracle.RELU),
+                                     (40, 60, BF16_RELU), (40, 17, BF16_SIGMOID)])
 def test_literal_and_incremental_samplers_agree(n, h, act):
     """Algorithm 1 taken literally and its incremental form give the same
     samples on shared uniforms (barring near-ties) and the same log pi."""
