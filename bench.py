@@ -206,6 +206,7 @@ def _oracle_iteration(cfg, inst, Bsub, theta, it):
     P = oracle.theta_to_made(theta, n, h)
     U = oracle.uniforms(Bsub, n, 12345, it)
     act = oracle.RELU if cfg["act"] == "relu" else oracle.SIGMOID
+    act |= oracle.HIDDEN_BF16  # the workload runs the BF16 model
     S, _ = oracle.sample(P, U, act)
     (dW1, db1, dW2, db2), st, E = oracle.vqmc_grad(P, inst, S, act)
     g = oracle.made_to_theta(dW1, db1, dW2, db2)

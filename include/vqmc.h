@@ -66,13 +66,27 @@ typedef enum {
 
 enum { VQMC_ACT_RELU = 0, VQMC_ACT_SIGMOID = 1 };
 
-/* Precision of the model weights inside the kernels.  FP32: FP32 weights
- * and FP32 CUDA-core GEMMs.  BF16: BF16 copies of W1, W2 (rounded to nearest
- * even from the FP32 master after every update) with FP32 accumulation; the
- * sampler still accumulates in FP32; the log-prob/backward GEMMs run on the
- * tcgen05 tensor cores with BF16 operands.  The master theta, Adam state and
+/* Precision of the model inside the kernels.  FP32: FP32 weights and
+ * activations, FP32 CUDA-core GEMMs.  BF16: the model has BF16 copies of W1,
+ * W2 (rounded to nearest even from the FP32 master after every update) and
+ * its hidden activations rounded to BF16 before the output layer, with FP32
+ * accumulation everywhere; the log-prob/backward GEMMs run on the tcgen05
+ * tensor cores with BF16 operands.  The master theta, Adam state and
  * gradients are FP32 in both modes; batch statistics are FP64. */
 enum { VQMC_PREC_FP32 = 0, VQMC_PREC_BF16 = 1 };
+
+/* Sampler implementation (vqmc_config.sampler).  Both draw the same exact
+ * samples of the model (Algorithm 1) from the same uniforms.
+ *   AUTO: TENSOR_CORE where it applies, else CUDA_CORE.
+ *   CUDA_CORE: one step at a time, FP32 FMAs on the CUDA cores; any model.
+ *   TENSOR_CORE: blocks of 64 or 128 steps whose bulk work (the logits from
+ *     hidden units completed before the block, and the update of hidden
+ *     units by the block's spins) runs as tcgen05 GEMMs, with a sequential
+ *     solver for the units that complete inside the block.  BF16 precision
+ *     only, h <= 2048, and at most 32 hidden units completing within 64
+ *     consecutive steps (h up to about n/2); vqmc_create returns UNSUPPORTED
+ *     when it is requested for any other model. */
+enum { VQMC_SAMPLER_AUTO = 0, VQMC_SAMPLER_CUDA_CORE = 1, VQMC_SAMPLER_TENSOR_CORE = 2 };
 
 /* Hamiltonian storage. */
 enum {
@@ -97,7 +111,7 @@ typedef struct {
   float beta1;        /* Adam beta1 (0.9) */
   float beta2;        /* Adam beta2 (0.999) */
   float eps;          /* Adam epsilon (1e-8) */
-  uint32_t reserved;
+  uint32_t sampler;   /* VQMC_SAMPLER_* (0 = AUTO) */
   uint64_t seed;      /* Philox4x32-10 key for the internal uniforms */
 } vqmc_config;
 

@@ -56,6 +56,7 @@ struct vqmc_ctx {
   int np, hp, Bp;  // padded n, h, batch
   int act, prec;   // VQMC_ACT_*, VQMC_PREC_*
   int ham;         // VQMC_HAM_*
+  int sampler;     // VQMC_SAMPLER_CUDA_CORE or _TENSOR_CORE (resolved at create)
   int nnz;
   int64_t d;
   uint64_t inst_hash = 0;
@@ -124,6 +125,11 @@ namespace vqmc {
 cudaError_t launch_uniforms(int B, int n, uint64_t seed, uint64_t iteration, float* d_u, cudaStream_t st);
 cudaError_t launch_sampler(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,
                            float* d_logp, cudaStream_t st);
+// ---- sampler_tc.cu: block size of the tensor-core sampler for this model, 0
+// if it does not apply; its launcher
+int sampler_tc_block(const vqmc_ctx* c);
+cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,
+                              float* d_logp, cudaStream_t st);
 
 // ---- eloc.cu
 cudaError_t launch_eloc_sparse(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st);

@@ -22,6 +22,7 @@
 #include <mutex>
 
 #include "gemm.cuh"
+#include "tc_ptx.cuh"
 
 namespace vqmc {
 namespace {
@@ -33,93 +34,10 @@ constexpr int STAGE_BYTES = TILE_A_BYTES + TILE_B_BYTES;
 constexpr int TMEM_COLS = BN;  // FP32 accumulator: 128 lanes x BN columns
 constexpr int SMEM_BYTES = 1024 /*alignment slack*/ + NSTAGE * STAGE_BYTES + 256 /*barriers*/ + 4 * BN * 4;
 
-// ------------------------------------------------------------------ PTX
+using namespace tc;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t* err) {
-  for (long long it = 0; it < kSpinLimit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  if (err) atomicOr(err, kErrTimeout);
-  return false;
-}
-
-// 2D tiled TMA load: box at (x = inner/K element, y = row) into smem, completing
-// transaction bytes on bar.  x is always a multiple of 64 elements.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-// UMMA shared-memory descriptor of a K-major operand tile written by TMA with
-// 128-byte swizzle: rows of 128 bytes (64 BF16 along K), 8-row groups 1024
-// bytes apart (stride byte offset), leading byte offset unused (1), version 1
-// (bits 46-47), layout SWIZZLE_128B (2, bits 61-63).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
-  return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
-// 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 16 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
-}
+// Instruction descriptor of the 128 x 128 tile.
+constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
 __device__ __forceinline__ float log_sigmoidf_(float x) {
@@ -203,15 +121,10 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
     mbar_init(smem_u32(done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
+  if (warp == 0) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+  fence_before();
   __syncthreads();
-  tc_fence_after();
+  fence_after();
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
 
@@ -234,12 +147,12 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
       const int s = it % NSTAGE;
       ok = mbar_wait(smem_u32(&full[s]), (uint32_t)((it / NSTAGE) & 1), err);
       if (!ok) break;
-      tc_fence_after();
+      fence_after();
       const uint32_t sa = base + s * STAGE_BYTES, sb = sa + TILE_A_BYTES;
       const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
 #pragma unroll
       for (int k = 0; k < BK / 16; ++k)  // advance 16 BF16 = 32 bytes along K inside the swizzle atom
-        mma_bf16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), (it > 0 || k > 0) ? 1u : 0u);
+        mma_bf16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kIdesc, (it > 0 || k > 0) ? 1u : 0u);
       mma_commit(smem_u32(&empty[s]));
     }
     if (nkt > 0 && ok) mma_commit(smem_u32(done));
@@ -250,7 +163,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
   // ----------------------------------------------------------- epilogue
   const bool done_ok = mbar_wait(smem_u32(done), 0u, err);
   __syncwarp();
-  tc_fence_after();
+  fence_after();
   const int m = m0 + warp * 32 + lane;  // this thread's tile row
   const bool mvalid = m < g.M;
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
@@ -319,15 +232,15 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
     }
   }
   if (g.row_part && (op == kOpOut || op == kOpEloc) && mvalid) g.row_part[(size_t)blockIdx.x * g.ldr + m] = rowsum;
-  tc_fence_before();
+  fence_before();
   __syncthreads();
   if (want_col && tid < BN && n0 + tid < g.N) {
     const float v = colbuf[tid] + colbuf[BN + tid] + colbuf[2 * BN + tid] + colbuf[3 * BN + tid];
     g.col_part[(size_t)blockIdx.y * g.ldc + n0 + tid] = v;
   }
   if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
   }
 }
 
@@ -354,20 +267,23 @@ void init_once() {
     g_have_tc = false;
 }
 
-// rows x cols (cols contiguous, leading dimension ld elements) BF16 matrix,
-// boxes of 64 columns x 128 rows, 128-byte swizzle, zero fill outside.
 bool encode(CUtensorMap* map, const void* ptr, int rows, int cols, int ld) {
+  return tc_encode_bf16(map, ptr, rows, cols, ld, BM);
+}
+
+}  // namespace
+
+bool tc_encode_bf16(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows) {
+  if (!gemm_tc_available()) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
-
-}  // namespace
 
 bool gemm_tc_available() {
   std::call_once(g_once, init_once);

@@ -60,6 +60,7 @@ cudaError_t launch_uniforms(int B, int n, uint64_t seed, uint64_t iteration, flo
 cudaError_t launch_sampler(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,
                            float* d_logp, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
+  if (c->sampler == VQMC_SAMPLER_TENSOR_CORE) return launch_sampler_tc(c, B, d_u, iteration, d_s, d_logp, st);
   SamplerArgs a;
   a.n = c->n;
   a.h = c->h;

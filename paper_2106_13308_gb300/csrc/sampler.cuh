@@ -51,6 +51,18 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // 24 high bits -> [0, 1) on the 2^-24 grid (exact in float).
 __device__ __forceinline__ float to_unit(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
 
+// logit(u) = log(u / (1 - u)); -inf at u = 0.  u < sigma(z) iff z > logit(u).
+__device__ __forceinline__ float logit(float u) { return logf(u) - log1pf(-u); }
+
+__device__ __forceinline__ float act_f(int act, float x) {
+  return act == VQMC_ACT_RELU ? fmaxf(x, 0.0f) : 1.0f / (1.0f + expf(-x));
+}
+
+// log sigma(x) without overflow.
+__device__ __forceinline__ float log_sigmoid(float x) {
+  return x >= 0.0f ? -log1pf(expf(-x)) : x - log1pf(expf(x));
+}
+
 }  // namespace
 
 }  // namespace vqmc

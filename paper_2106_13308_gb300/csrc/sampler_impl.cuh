@@ -68,19 +68,8 @@ __device__ __forceinline__ float from_f<float>(float x) { return x; }
 template <>
 __device__ __forceinline__ bf16 from_f<bf16>(float x) { return __float2bfloat16_rn(x); }
 
-__device__ __forceinline__ float act_f(int act, float x) {
-  return act == VQMC_ACT_RELU ? fmaxf(x, 0.0f) : 1.0f / (1.0f + expf(-x));
-}
-
-// log sigma(x) without overflow.
-__device__ __forceinline__ float log_sigmoid(float x) {
-  return x >= 0.0f ? -log1pf(expf(-x)) : x - log1pf(expf(x));
-}
-
 constexpr int kBig = 0x3fffffff;
 
-// logit(u) = log(u / (1 - u)); -inf at u = 0.  u < sigma(z) iff z > logit(u).
-__device__ __forceinline__ float logit(float u) { return logf(u) - log1pf(-u); }
 
 // ---- packed FP32 pairs (fma.rn.f32x2: two IEEE FP32 FMAs in one instruction)
 __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
@@ -148,6 +137,14 @@ struct Sampler {
 
   static __device__ __forceinline__ int deg(int k, int n, int h) { return k < h ? degree(k, n, h) : kBig; }
 
+  // hidden activation as the output layer sees it: rounded to bfloat16 in
+  // the BF16 model (as the BF16 forward GEMM stores it), exact in FP32
+  static __device__ __forceinline__ float g1(int g_act, float a) {
+    const float g = act_f(g_act, a);
+    if constexpr (sizeof(WT) == 2) return __bfloat162float(__float2bfloat16_rn(g));
+    else return g;
+  }
+
   // Mixed slot: the lane's two units may be in different roles.  Weights of
   // units that must not take part are zeroed, so the pair still runs as f32x2.
   // (At i = 1 the spins are still zero, so the update adds nothing.)
@@ -165,8 +162,8 @@ struct Sampler {
       for (int s = 0; s < SL; ++s) {
         float a0, a1;
         unpack2(st.a[r][s], a0, a1);
-        if (m0 == i - 1) a0 = act_f(g_act, a0);
-        if (m1 == i - 1) a1 = act_f(g_act, a1);
+        if (m0 == i - 1) a0 = g1(g_act, a0);
+        if (m1 == i - 1) a1 = g1(g_act, a1);
         st.a[r][s] = pack2(a0, a1);
       }
     }

@@ -1,0 +1,446 @@
+// Blocked autoregressive sampler on the tcgen05 tensor cores, for the BF16
+// model (BF16 weights, hidden activations rounded to BF16, FP32 accumulation).
+//
+// Algorithm 1 draws s_1 .. s_n in order; with the incremental forward pass
+// (Sec. 2.3) the logit of step i is
+//     z_i = b2_i + sum_{k : m(k) < i} W2_ik g1_k,
+//     g1_k = act(b1_k + sum_{j <= m(k)} W1_kj s_j),
+// and with sorted degrees a hidden unit is complete once s_{m(k)} is drawn.
+// This kernel processes the n steps in blocks of D (64 or 128).  For block
+// [i0, i0 + D):
+//   * units complete before the block (m(k) < i0, a prefix of the units)
+//     feed every output of the block through one tensor-core GEMM,
+//         Z[i][s] = sum_k W2[i][k] g1[k][s]     (M = 128 outputs, N = 16
+//     samples, K = that prefix), with g1 kept in shared memory in BF16;
+//   * the few units completing inside the block (m(k) in [i0, i0 + D), at
+//     most 32: the "recent" units) are carried by a small sequential solver
+//     that draws the D spins: z_i = Z[i] + b2_i + sum_recent W2_ik g1_k, with
+//     each recent pre-activation extended by W1_ki s_i after every draw;
+//   * the block's spins then update every unit still incomplete by a second
+//     tensor-core GEMM, A[k][s] += sum_j W1[k][j] s_j over the block's inputs
+//     (M = 128 units, N = 16, K = D), into FP32 accumulators that stay in
+//     tensor memory for the whole run (16 columns per 128 units).
+// The masks need no special handling: masked weights are stored as zeros, so
+// an update adds nothing to a complete unit and an incomplete unit (g1 = 0
+// in shared memory until it completes) adds nothing to any logit.
+//
+// CTA = 16 samples, 6 warps: warps 0-3 own TMEM lanes 32w..32w+31 (read Z
+// and the recent pre-activations, prepare the block's logits and recent
+// weights, write the spins); warps 0-1 are the solver (4 lanes per sample,
+// 8 recent units per lane); warp 4 lane 0 streams 128 x 64 BF16 weight tiles
+// with TMA into a 6-stage ring; warp 5 lane 0 issues the MMAs.  Every wait is
+// bounded; after a failed wait the CTA raises the timeout bit and runs on
+// without waiting, so it still finishes.
+#include <algorithm>
+
+#include "gemm.cuh"
+#include "sampler.cuh"
+#include "tc_ptx.cuh"
+
+namespace vqmc {
+namespace {
+
+using namespace tc;
+
+constexpr int kS = 16;                     // samples per CTA (MMA N)
+constexpr int kRmax = 32;                  // recent units per block
+constexpr int kNStage = 6;                 // weight ring stages
+constexpr int kTileBytes = 128 * 64 * 2;   // one 128 x 64 BF16 tile
+constexpr int kMaxHp = 2048;               // hidden units (padded) in TMEM
+constexpr int kDmax = 128;
+constexpr int kTmemCols = 512;             // A: 16 per 128 units (<= 256), Z at 256
+constexpr int kZCol = 256;
+constexpr int kThreads = 192;
+constexpr int kZld = kS + 1;               // padded row of the Z buffer
+constexpr uint32_t kIdesc = idesc_bf16(128, kS);
+
+// shared memory map (offsets from a 1024-byte aligned base)
+constexpr int kOffRing = 0;
+constexpr int kOffH = kOffRing + kNStage * kTileBytes;         // g1, [hp/64] x (16 x 64) swizzled
+constexpr int kOffS = kOffH + (kMaxHp / 64) * 2048;            // spins, [D/64] x (16 x 64) swizzled
+constexpr int kOffZ = kOffS + (kDmax / 64) * 2048;             // Z [D][kZld] float
+constexpr int kOffLG = kOffZ + kDmax * kZld * 4;               // logit(u) [D][16] float
+constexpr int kOffP = kOffLG + kDmax * kS * 4;                 // recent pre-activations [32][16] float
+constexpr int kOffWr = kOffP + kRmax * kS * 4;                 // W1 of recent units [D][32] bf16
+constexpr int kOffVr = kOffWr + kDmax * kRmax * 2;             // W2 of recent units [D][32] bf16
+constexpr int kOffB2 = kOffVr + kDmax * kRmax * 2;             // b2 [D] float
+constexpr int kOffS8 = kOffB2 + kDmax * 4;                     // spins [16][D] int8
+constexpr int kOffBar = kOffS8 + kS * kDmax;                   // mbarriers + slots
+constexpr int kSmemBytes = 1024 + kOffBar + 256;
+
+struct TcArgs {
+  int n, h, hp, B, D, act;
+  const bf16* wt;     // wt_s [rows][hp]: row j = W1[:, j] (input j)
+  const bf16* v;      // v_s  [rows][hp]: row r = W2[r] (output r + 1)
+  const float* b1;
+  const float* b2;
+  const float* u;     // [B][n] or null (internal Philox)
+  uint32_t key0, key1, it0, it1;
+  int8_t* s_out;      // [B][n]
+  float* logp;        // [B] or null
+  uint32_t* err;
+};
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+// bounded wait that gives up at once after any failure in the CTA
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t* err) {
+  if (*abort) return false;
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 255 && *abort) return false;
+  }
+  atomicOr(err, kErrTimeout);
+  *abort = 1;
+  return false;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    sampler_tc_kernel(const __grid_constant__ CUtensorMap mapV, const __grid_constant__ CUtensorMap mapW,
+                      const TcArgs g) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* sm = smem_raw + (base - raw);
+  unsigned char* Hs = sm + kOffH;
+  unsigned char* Ss = sm + kOffS;
+  float* Zs = reinterpret_cast<float*>(sm + kOffZ);
+  float* LG = reinterpret_cast<float*>(sm + kOffLG);
+  float* Pr = reinterpret_cast<float*>(sm + kOffP);
+  bf16* Wr = reinterpret_cast<bf16*>(sm + kOffWr);
+  bf16* Vr = reinterpret_cast<bf16*>(sm + kOffVr);
+  float* b2s = reinterpret_cast<float*>(sm + kOffB2);
+  int8_t* S8 = reinterpret_cast<int8_t*>(sm + kOffS8);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kOffBar);
+  uint64_t* empty = full + kNStage;
+  uint64_t* zfull = empty + kNStage;
+  uint64_t* ready = zfull + 1;
+  uint64_t* drain = ready + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = g.n, h = g.h, D = g.D;
+  const int nblk = (n + D - 1) / D;
+  const int ntiles = (g.hp + 127) / 128;
+  const int nkd = D / 64;
+  const int b0 = blockIdx.x * kS;
+
+  if (tid == 0) {
+    for (int s = 0; s < kNStage; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(zfull), 1);
+    mbar_init(smem_u32(ready), 128);
+    mbar_init(smem_u32(drain), 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 5) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+  // g1 of every unit is zero until the unit completes; spins start at zero
+  for (int q = tid; q < (kOffZ - kOffH) / 16; q += kThreads) reinterpret_cast<uint4*>(Hs)[q] = make_uint4(0, 0, 0, 0);
+  fence_proxy_async();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // A = b1 for every sample
+  if (warp < 4) {
+    for (int t = 0; t < ntiles; ++t) {
+      const int k = 128 * t + 32 * warp + lane;
+      const float x = k < h ? g.b1[k] : 0.0f;
+      float v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = x;
+      tmem_st16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * t), v);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+
+  if (warp == 4) {
+    // ----------------------------------------------------------- producer
+    if (lane == 0) {
+      int it = 0;
+      auto load = [&](const CUtensorMap* map, int x, int y) -> bool {
+        const int s = it % kNStage;
+        if (it >= kNStage && !wait_or_abort(smem_u32(&empty[s]), (uint32_t)((it / kNStage - 1) & 1), abort, g.err))
+          return false;
+        const uint32_t bar = smem_u32(&full[s]);
+        mbar_expect_tx(bar, kTileBytes);
+        tma_load_2d(base + kOffRing + s * kTileBytes, map, x, y, bar);
+        ++it;
+        return true;
+      };
+      bool ok = true;
+      for (int b = 0; b < nblk && ok; ++b) {
+        const int klo = count_deg_le(b * D, n, h);  // units complete before block b
+        if (b > 0)  // W1 tiles for block b-1's inputs, units not yet complete
+          for (int t = klo / 128; t < ntiles && ok; ++t)
+            for (int kk = 0; kk < nkd && ok; ++kk) ok = load(&mapW, (b - 1) * D + 64 * kk, 128 * t);
+        const int nc = (klo + 63) / 64;  // W2 tiles: block rows x complete units
+        for (int c = 0; c < nc && ok; ++c) ok = load(&mapV, 64 * c, b * D);
+      }
+      // no copy may still be landing when the CTA exits (after a failure
+      // some loaded tiles are never consumed)
+      for (int p = it > kNStage ? it - kNStage : 0; p < it; ++p)
+        mbar_wait(smem_u32(&full[p % kNStage]), (uint32_t)((p / kNStage) & 1), g.err);
+    }
+  } else if (warp == 5) {
+    // --------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      auto take = [&]() -> uint32_t {  // next full ring stage (smem address), or 0
+        const int s = it % kNStage;
+        if (!wait_or_abort(smem_u32(&full[s]), (uint32_t)((it / kNStage) & 1), abort, g.err)) return 0;
+        fence_after();
+        return base + kOffRing + s * kTileBytes;
+      };
+      for (int b = 0; b < nblk; ++b) {
+        const int klo = count_deg_le(b * D, n, h);
+        bool issued = false;
+        if (b > 0 && ok) {
+          ok = wait_or_abort(smem_u32(ready), (uint32_t)((b - 1) & 1), abort, g.err);
+          fence_after();
+          for (int t = klo / 128; t < ntiles && ok; ++t)
+            for (int kk = 0; kk < nkd && ok; ++kk) {
+              const uint32_t a = take();
+              if (!a) {
+                ok = false;
+                break;
+              }
+              const uint64_t da = smem_desc_sw128(a), db = smem_desc_sw128(base + kOffS + kk * 2048);
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                mma_bf16(tmem + (uint32_t)(16 * t), da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kIdesc, 1u);
+              mma_commit(smem_u32(&empty[it % kNStage]));
+              ++it;
+              issued = true;
+            }
+        }
+        const int nc = (klo + 63) / 64;
+        for (int c = 0; c < nc && ok; ++c) {
+          const uint32_t a = take();
+          if (!a) {
+            ok = false;
+            break;
+          }
+          const uint64_t da = smem_desc_sw128(a), db = smem_desc_sw128(base + kOffH + c * 2048);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            mma_bf16(tmem + kZCol, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kIdesc, (c > 0 || k > 0) ? 1u : 0u);
+          mma_commit(smem_u32(&empty[it % kNStage]));
+          ++it;
+          issued = true;
+        }
+        if (ok && issued) mma_commit(smem_u32(zfull));
+        else mbar_arrive(smem_u32(zfull));
+      }
+      // every MMA has completed before tensor memory is released
+      mma_commit(smem_u32(drain));
+      mbar_wait(smem_u32(drain), 0u, g.err);
+    }
+  } else {
+    // ------------------------------------------- warps 0-3: blocks, solver
+    const int s_me = tid >> 2, sub = tid & 3;  // solver lanes (tid < 64)
+    float lp = 0.0f;
+    const uint32_t tq = tmem + ((uint32_t)(32 * warp) << 16);
+    for (int b = 0; b < nblk; ++b) {
+      const int i0 = b * D + 1;  // first output (1-based)
+      const int klo = count_deg_le(b * D, n, h), khi = count_deg_le(b * D + D, n, h);
+      const int R = khi - klo;  // <= kRmax (checked by the host)
+      const int steps = min(D, n - b * D);
+      // (a) the block's inputs, while the GEMM runs
+      for (int e = tid; e < D; e += 128) b2s[e] = e < steps ? g.b2[b * D + e] : 0.0f;
+      for (int q = tid; q < kS * (D / 4); q += 128) {
+        const int s = q % kS, t = b * D + 4 * (q / kS);
+        const int bb = b0 + s;
+        float* dst = LG + (size_t)(4 * (q / kS)) * kS + s;
+        if (g.u) {
+#pragma unroll
+          for (int w = 0; w < 4; ++w)
+            dst[w * kS] = (bb < g.B && t + w < n) ? logit(__ldg(g.u + (size_t)bb * n + t + w)) : 0.0f;
+        } else {
+          const uint4 r = philox4x32_10(make_uint4((uint32_t)(t >> 2), (uint32_t)bb, g.it0, g.it1), g.key0, g.key1);
+          dst[0] = logit(to_unit(r.x));
+          dst[kS] = logit(to_unit(r.y));
+          dst[2 * kS] = logit(to_unit(r.z));
+          dst[3 * kS] = logit(to_unit(r.w));
+        }
+      }
+      for (int q = tid; q < D * kRmax; q += 128) {
+        const int e = q / kRmax, r = q % kRmax;
+        const bool in = r < R && e < steps;
+        Vr[q] = in ? g.v[(size_t)(b * D + e) * g.hp + klo + r] : __float2bfloat16_rn(0.0f);  // W2[i0+e][k]
+        Wr[q] = in ? g.wt[(size_t)(i0 + e) * g.hp + klo + r] : __float2bfloat16_rn(0.0f);   // W1[k][i0+e]
+      }
+      for (int q = tid; q < (kRmax - R) * kS; q += 128) Pr[R * kS + q] = 0.0f;
+      // (b) Z and the recent pre-activations from tensor memory
+      const int nc = (klo + 63) / 64;
+      wait_or_abort(smem_u32(zfull), (uint32_t)(b & 1), abort, g.err);
+      __syncwarp();
+      fence_after();
+      // warp-uniform: tcgen05.ld is executed by all lanes of a warp or none
+      const bool live = !__any_sync(0xffffffffu, *abort != 0);
+      {
+        float v[16];
+        if (nc > 0 && live) {
+          tmem_ld16(tq + kZCol, v);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+        }
+        const int e = 32 * warp + lane;
+        if (e < D) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) Zs[e * kZld + q] = v[q];
+        }
+      }
+      if (R > 0 && live) {
+        for (int t = klo / 128; t <= (khi - 1) / 128; ++t) {
+          float v[16];
+          tmem_ld16(tq + (uint32_t)(16 * t), v);
+          const int k = 128 * t + 32 * warp + lane;
+          if (k >= klo && k < khi) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) Pr[(k - klo) * kS + q] = v[q];
+          }
+        }
+      }
+      fence_before();
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      // (c) the D draws of the block (warps 0-1)
+      if (warp < 2) {
+        float pre[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pre[j] = Pr[(8 * sub + j) * kS + s_me];
+        const int act = g.act;
+        for (int e = 0; e < steps; ++e) {
+          const uint4 vv = *reinterpret_cast<const uint4*>(Vr + e * kRmax + 8 * sub);
+          const uint32_t vw[4] = {vv.x, vv.y, vv.z, vv.w};
+          float z0 = 0.0f, z1 = 0.0f;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            z0 = fmaf(bf_lo(vw[q]), bf16r(act_f(act, pre[2 * q])), z0);
+            z1 = fmaf(bf_hi(vw[q]), bf16r(act_f(act, pre[2 * q + 1])), z1);
+          }
+          float zp = z0 + z1;
+          zp += __shfl_xor_sync(0xffffffffu, zp, 1);
+          zp += __shfl_xor_sync(0xffffffffu, zp, 2);
+          const float z = Zs[e * kZld + s_me] + b2s[e] + zp;
+          const bool up = z > LG[e * kS + s_me];  // u < sigma(z)
+          const float sv = up ? 1.0f : -1.0f;
+          const uint4 ww = *reinterpret_cast<const uint4*>(Wr + e * kRmax + 8 * sub);
+          const uint32_t wv[4] = {ww.x, ww.y, ww.z, ww.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            pre[2 * q] = fmaf(bf_lo(wv[q]), sv, pre[2 * q]);
+            pre[2 * q + 1] = fmaf(bf_hi(wv[q]), sv, pre[2 * q + 1]);
+          }
+          if (sub == 0) {
+            S8[s_me * kDmax + e] = up ? (int8_t)1 : (int8_t)-1;
+            if (g.logp) lp += log_sigmoid(up ? z : -z);
+          }
+        }
+        // the recent units are now complete: their g1 joins the GEMM operand
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int r = 8 * sub + j;
+          if (r < R) {
+            const int k = klo + r;
+            *reinterpret_cast<bf16*>(Hs + (k >> 6) * 2048 + sw128_offset(s_me, k & 63)) =
+                __float2bfloat16_rn(act_f(act, pre[j]));
+          }
+        }
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      // (d) spins: GEMM operand for the update, and the output
+      for (int q = tid; q < kS * D; q += 128) {
+        const int s = q / D, e = q % D;
+        const int8_t y = S8[s * kDmax + e];
+        *reinterpret_cast<bf16*>(Ss + (e >> 6) * 2048 + sw128_offset(s, e & 63)) =
+            __float2bfloat16_rn(y > 0 ? 1.0f : -1.0f);
+        const int bb = b0 + s;
+        if (bb < g.B && e < steps) g.s_out[(size_t)bb * n + b * D + e] = y > 0 ? (int8_t)1 : (int8_t)-1;
+      }
+      fence_proxy_async();
+      fence_before();
+      mbar_arrive(smem_u32(ready));
+    }
+    if (tid < 64 && sub == 0 && g.logp && b0 + s_me < g.B && !*abort) g.logp[b0 + s_me] = lp;
+  }
+
+  __syncwarp();
+  fence_before();
+  __syncthreads();
+  if (warp == 5) {
+    __syncwarp();
+    fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+bool g_attr_set = false;
+
+// largest number of units completing inside one block of D steps
+int max_recent(int n, int h, int D) {
+  int r = 0;
+  for (int b = 0; b * D < n; ++b) r = std::max(r, count_deg_le(b * D + D, n, h) - count_deg_le(b * D, n, h));
+  return r;
+}
+
+}  // namespace
+
+// Block size the tensor-core sampler would use for this model, or 0 when it
+// does not apply (FP32 weights, more than 2048 hidden units, or more than
+// 32 units completing within every block size).
+int sampler_tc_block(const vqmc_ctx* c) {
+  if (c->prec != VQMC_PREC_BF16 || c->hp > kMaxHp) return 0;
+  for (int D : {128, 64})
+    if (max_recent(c->n, c->h, D) <= kRmax) return D;
+  return 0;
+}
+
+cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,
+                              float* d_logp, cudaStream_t st) {
+  const int D = sampler_tc_block(c);
+  if (D == 0 || !gemm_tc_available()) return cudaErrorNotSupported;
+  if (B <= 0) return cudaSuccess;
+  CUtensorMap mapV, mapW;
+  if (!tc_encode_bf16(&mapV, c->v_s, sampler_rows(c->n), c->hp, c->hp, 128) ||
+      !tc_encode_bf16(&mapW, c->w_s, c->h, c->np, c->np, 128))
+    return cudaErrorInvalidValue;
+  if (!g_attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(sampler_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    g_attr_set = true;
+  }
+  TcArgs a;
+  a.n = c->n;
+  a.h = c->h;
+  a.hp = c->hp;
+  a.B = B;
+  a.D = D;
+  a.act = c->act;
+  a.wt = reinterpret_cast<const bf16*>(c->wt_s);
+  a.v = reinterpret_cast<const bf16*>(c->v_s);
+  a.b1 = c->b1;
+  a.b2 = c->b2;
+  a.u = d_u;
+  a.key0 = (uint32_t)c->cfg.seed;
+  a.key1 = (uint32_t)(c->cfg.seed >> 32);
+  a.it0 = (uint32_t)iteration;
+  a.it1 = (uint32_t)(iteration >> 32);
+  a.s_out = d_s;
+  a.logp = d_logp;
+  a.err = c->err;
+  sampler_tc_kernel<<<(B + kS - 1) / kS, kThreads, kSmemBytes, st>>>(mapV, mapW, a);
+  return cudaGetLastError();
+}
+
+}  // namespace vqmc

@@ -198,6 +198,7 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
     return fail(VQMC_ERR_INVALID_ARG, "bad instance kind");
   }
   if (pad_up(h) > 2048) return fail(VQMC_ERR_UNSUPPORTED, "this build samples with h <= 2048");
+  if (cfg->sampler > VQMC_SAMPLER_TENSOR_CORE) return fail(VQMC_ERR_INVALID_ARG, "bad sampler");
 
   vqmc_ctx* c = new vqmc_ctx();
   c->cfg = *cfg;
@@ -210,6 +211,15 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
     vqmc_destroy(c);
     return fail(s, m);
   };
+  {
+    const bool tc_ok = sampler_tc_block(c) > 0 && gemm_tc_available();
+    if (cfg->sampler == VQMC_SAMPLER_TENSOR_CORE && !tc_ok)
+      return cleanup_fail(VQMC_ERR_UNSUPPORTED,
+                          "tensor-core sampler needs BF16, a tcgen05 device and at most 32 hidden units "
+                          "completing within 64 steps");
+    c->sampler = (cfg->sampler != VQMC_SAMPLER_CUDA_CORE && tc_ok) ? VQMC_SAMPLER_TENSOR_CORE
+                                                                      : VQMC_SAMPLER_CUDA_CORE;
+  }
 #define VQ_ALLOC(ptr, bytes)                                                                         \
   do {                                                                                               \
     cudaError_t e_ = dalloc(&(ptr), (bytes));                                                        \
@@ -288,7 +298,6 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
       return cleanup_fail(VQMC_ERR_CUDA, "copy of the field failed");
     hsh = fnv1a(hsh, inst->field, (size_t)n * 4);
   }
-  c->cfg.reserved = 0;
   c->inst_hash = hsh;
   if (launch_refresh_weights(c, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
     return cleanup_fail(VQMC_ERR_CUDA, "initial weight refresh failed");

@@ -25,6 +25,7 @@ VQMC_OK, VQMC_ERR_INVALID_ARG, VQMC_ERR_CUDA, VQMC_ERR_OOM = 0, 1, 2, 3
 VQMC_ERR_NONFINITE, VQMC_ERR_TIMEOUT, VQMC_ERR_UNSUPPORTED = 4, 5, 6
 ACT = {"relu": 0, "sigmoid": 1}
 PREC = {"fp32": 0, "bf16": 1}
+SAMPLER = {"auto": 0, "cuda_core": 1, "tensor_core": 2}
 HAM = {"sparse_i32": 0, "sparse_f32": 1, "dense": 2}
 DEVERR_TIMEOUT, DEVERR_NONFINITE = 1, 2
 
@@ -49,7 +50,7 @@ class Config(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("h", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("act", ctypes.c_int32), ("precision", ctypes.c_int32), ("lr", ctypes.c_float),
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
-                ("reserved", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+                ("sampler", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
 
 
 class Instance(ctypes.Structure):
@@ -253,13 +254,13 @@ class VQMC:
     J)."""
 
     def __init__(self, n, h, max_batch, instance, act="relu", precision="bf16", lr=1e-2, beta1=0.9,
-                 beta2=0.999, eps=1e-8, seed=0):
+                 beta2=0.999, eps=1e-8, seed=0, sampler="auto"):
         load_library()
         self.n, self.h, self.max_batch = int(n), int(h), int(max_batch)
         self.act, self.precision = act, precision
         self.kind = instance["kind"]
-        cfg = Config(self.n, self.h, self.max_batch, ACT[act], PREC[precision], lr, beta1, beta2, eps, 0,
-                     int(seed) & (2 ** 64 - 1))
+        cfg = Config(self.n, self.h, self.max_batch, ACT[act], PREC[precision], lr, beta1, beta2, eps,
+                     SAMPLER[sampler], int(seed) & (2 ** 64 - 1))
         keep = []
 
         def arr(a, dt):

@@ -14,6 +14,13 @@ from paper_2106_13308_gb300 import inputs
 ACT_ORACLE = {"relu": oracle.RELU, "sigmoid": oracle.SIGMOID}
 
 
+def act_code(act, precision="fp32"):
+    """Oracle activation code of the model a precision runs: the BF16 model
+    rounds hidden activations to bfloat16 (weights via oracle_params)."""
+    code = ACT_ORACLE[act] if isinstance(act, str) else int(act)
+    return code | (oracle.HIDDEN_BF16 if precision == "bf16" else 0)
+
+
 def build_lib():
     from paper_2106_13308_gb300 import build
     build.build()
@@ -54,7 +61,7 @@ def sigmoid(x):
 def teacher_forced(P, S, U, act, tol=1e-6):
     """(mismatches, near_ties): every spin with |u - p_i| >= tol must equal
     [u < p_i] where p_i is the oracle's conditional on the sample's own prefix."""
-    Z = oracle.logits(P, S, ACT_ORACLE[act])
+    Z = oracle.logits(P, S, act_code(act))
     p = sigmoid(Z)
     U = np.asarray(U, dtype=np.float64)
     decided = np.abs(U - p) >= tol
@@ -63,7 +70,7 @@ def teacher_forced(P, S, U, act, tol=1e-6):
 
 
 def rows_without_near_ties(P, S_oracle, U, act, tol=1e-6):
-    Z = oracle.logits(P, S_oracle, ACT_ORACLE[act])
+    Z = oracle.logits(P, S_oracle, act_code(act))
     return ~(np.abs(np.asarray(U, np.float64) - sigmoid(Z)) < tol).any(axis=1)
 
 
@@ -74,9 +81,9 @@ def rel_err(a, b):
     return float(np.linalg.norm(a - b) / (den if den > 0 else 1.0))
 
 
-def make_model(n, h, B, inst, act="relu", precision="fp32", theta=None, seed=123, lr=1e-2):
+def make_model(n, h, B, inst, act="relu", precision="fp32", theta=None, seed=123, lr=1e-2, sampler="auto"):
     from paper_2106_13308_gb300.vqmc import VQMC
-    m = VQMC(n, h, B, inst, act=act, precision=precision, seed=seed, lr=lr)
+    m = VQMC(n, h, B, inst, act=act, precision=precision, seed=seed, lr=lr, sampler=sampler)
     if theta is not None:
         m.set_params(torch.from_numpy(np.asarray(theta, dtype=np.float32)))
     return m

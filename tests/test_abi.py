@@ -44,7 +44,7 @@ def test_struct_layouts_match_header():
 
 def _cfg(vqmc, **kw):
     d = dict(n=10, h=8, max_batch=16, act=0, precision=1, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
-             reserved=0, seed=1)
+             sampler=0, seed=1)
     d.update(kw)
     return vqmc.Config(**d)
 

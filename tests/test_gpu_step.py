@@ -12,7 +12,7 @@ import oracle
 from paper_2106_13308_gb300 import inputs
 from paper_2106_13308_gb300.vqmc import StepStats
 
-from gpu_helpers import (ACT_ORACLE, build_lib, logp_rel, make_model, masked, oracle_params, rel_err,
+from gpu_helpers import (ACT_ORACLE, act_code, build_lib, logp_rel, make_model, masked, oracle_params, rel_err,
                          rows_without_near_ties, teacher_forced, er_instance)
 
 pytestmark = pytest.mark.gpu
@@ -157,15 +157,16 @@ def test_full_size_er10000_sampled_outputs(prec):
     assert np.array_equal(E.astype(np.float64), oracle.energy(inst, Sn))
     pick = np.array([0, 1, 777, 1024, 2046, 2047])
     U = oracle.uniforms(B, n, seed, 0)[pick]
-    mism, ties = teacher_forced(P, Sn[pick], U, "relu")
+    code = act_code("relu", prec)
+    mism, ties = teacher_forced(P, Sn[pick], U, code, 1e-6 if prec == "fp32" else 1e-4)
     assert mism == 0, (mism, ties)
-    lpo = oracle.logprob(P, Sn[pick])
-    assert logp_rel(lp.cpu().numpy()[pick], lpo) <= 1e-5
+    lpo = oracle.logprob(P, Sn[pick], code)
+    assert logp_rel(lp.cpu().numpy()[pick], lpo) <= (1e-5 if prec == "fp32" else 1e-3)
     lpg = m.logprob(S).cpu().numpy()[pick]
     assert logp_rel(lpg, lpo) <= (1e-5 if prec == "fp32" else 2e-2)
     gout = np.zeros(B, dtype=np.float32)
     gsel = pick[:4]
     gout[gsel] = np.array([0.5, -1.0, 0.25, 2.0], dtype=np.float32)
     g = m.logprob_backward(S, torch.from_numpy(gout).cuda()).cpu().numpy()
-    go = oracle.made_to_theta(*oracle.logprob_grad(P, Sn[gsel], gout[gsel].astype(np.float64)))
+    go = oracle.made_to_theta(*oracle.logprob_grad(P, Sn[gsel], gout[gsel].astype(np.float64), code))
     assert rel_err(g, go) <= (1e-4 if prec == "fp32" else 3e-2)
