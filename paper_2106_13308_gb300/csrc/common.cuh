@@ -96,6 +96,11 @@ struct vqmc_ctx {
 
   // workspaces (element type per precision unless noted)
   int8_t* S = nullptr;     // int8 [Bmax][n] samples of vqmc_step
+  uint32_t* Sbits = nullptr;  // sparse energy: [ceil(Bmax/32)][n] spins packed 32 samples per word
+  void* eloc_part = nullptr;  // [eloc_slices][Bmax] partial energies (int32/float)
+  int32_t* eloc_slice = nullptr;  // [eloc_slices + 1] first CSR row of each slice
+  int32_t* erow = nullptr;        // [nnz] CSR row of each edge
+  int eloc_slices = 1;
   void* E = nullptr;       // int32/float [Bmax]
   void* Sx = nullptr;      // [Bmax][np] spins as GEMM operand
   void* St = nullptr;      // [n][Bp] spins transposed

@@ -2,11 +2,14 @@
 // Eq. (eq:stochastic_variance)) and spin-layout conversions.
 //
 // Sparse local energy.  For a diagonal Hamiltonian l(s) = H_ss =
-// sum_{i<j} J_ij s_i s_j + sum_i h_i s_i.  One CTA handles 32 samples: it first
-// packs their spins bit-transposed into shared memory (bits[i] bit l = [s_i of
-// sample l is -1]), so one 32-bit xor of two words gives the sign of s_i s_j
-// for all 32 samples; then the warps split the CSR rows and lane l
-// accumulates sample l.  Integer weights accumulate in int32 (exact).
+// sum_{i<j} J_ij s_i s_j + sum_i h_i s_i.  The spins are first packed
+// bit-transposed, 32 samples per word: Sbits[w][i] bit l = [s_i of sample
+// 32w + l is -1] (one warp per 32 x 32 tile, coalesced reads).  Then one CTA
+// per (word, slice of rows) loads its n words into shared memory, so one
+// 32-bit xor of two words gives the sign of s_i s_j for all 32 samples, the
+// warps take the slice's CSR rows in turn and lane l accumulates sample l.
+// Slices hold about equal numbers of edges; their partial energies are summed
+// in slice order.  Integer weights accumulate in int32 (exact).
 #include "common.cuh"
 
 namespace vqmc {
@@ -14,46 +17,102 @@ namespace {
 
 constexpr int kElocWarps = 8;
 
+// Sbits[w][i] for a 32-site x 32-sample tile per warp.
+__global__ void __launch_bounds__(256) pack_bits_kernel(int B, int n, const int8_t* __restrict__ S,
+                                                        uint32_t* __restrict__ bits) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = (blockIdx.x * 8 + warp) * 32, w = blockIdx.y;
+  if (i0 >= n) return;
+  const int b = 32 * w + lane;
+  // lane l: bit i = [s_{i0+i} of sample b is -1]
+  uint32_t m = 0;
+  if (b < B) {
+    const int8_t* row = S + (size_t)b * n + i0;
+    const int cnt = min(32, n - i0);
+    if (cnt == 32 && (reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+      const uint4 q0 = __ldg(reinterpret_cast<const uint4*>(row)), q1 = __ldg(reinterpret_cast<const uint4*>(row) + 1);
+      const uint32_t wv[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        // sign bits of the 4 bytes of word k (spins are +-1: bit 7 set iff -1)
+        const uint32_t sg = (wv[k] >> 7) & 0x01010101u;
+        m |= ((sg * 0x01020408u) >> 24 & 0xFu) << (4 * k);
+      }
+    } else {
+      for (int i = 0; i < cnt; ++i) m |= (__ldg(row + i) < 0 ? 1u : 0u) << i;
+    }
+  }
+  uint32_t out = 0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const uint32_t t = __ballot_sync(0xffffffffu, (m >> i) & 1u);
+    if (lane == i) out = t;
+  }
+  if (i0 + lane < n) bits[(size_t)w * n + i0 + lane] = out;
+}
+
+// Edges of slice q are split evenly among the warps; each warp reads 32
+// edges at a time (row, column, weight) with coalesced loads and broadcasts
+// them with shuffles, so no load waits on another.
 template <typename W, typename A>
-__global__ void __launch_bounds__(kElocWarps * 32) eloc_sparse_kernel(int B, int n, const int8_t* __restrict__ S,
+__global__ void __launch_bounds__(kElocWarps * 32) eloc_sparse_kernel(int B, int n, const uint32_t* __restrict__ Sbits,
                                                                       const int32_t* __restrict__ row_ptr,
+                                                                      const int32_t* __restrict__ erow,
                                                                       const int32_t* __restrict__ col,
                                                                       const W* __restrict__ w,
-                                                                      const W* __restrict__ field, A* __restrict__ E) {
+                                                                      const W* __restrict__ field,
+                                                                      const int32_t* __restrict__ slice,
+                                                                      A* __restrict__ part, int ldp) {
   extern __shared__ uint32_t bits[];  // [n]
   __shared__ A red[kElocWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b0 = blockIdx.x * 32;
-  const int b = b0 + lane;
-  const int8_t* row = S + (size_t)(b < B ? b : b0) * n;
-  for (int i = warp; i < n; i += kElocWarps) {
-    const bool neg = b < B && __ldg(row + i) < 0;
-    const uint32_t m = __ballot_sync(0xffffffffu, neg);
-    if (lane == 0) bits[i] = m;
-  }
+  const int wd = blockIdx.x, q = blockIdx.y;
+  const uint32_t* src = Sbits + (size_t)wd * n;
+  for (int i = threadIdx.x; i < n; i += kElocWarps * 32) bits[i] = __ldg(src + i);
   __syncthreads();
   A e = 0;
-  for (int i = warp; i < n; i += kElocWarps) {
-    const uint32_t bi = bits[i];
-    if (field) {
+  const int r0 = __ldg(slice + q), r1 = __ldg(slice + q + 1);
+  if (field)
+    for (int i = r0 + warp; i < r1; i += kElocWarps) {
       const A f = (A)__ldg(field + i);
-      e += ((bi >> lane) & 1u) ? -f : f;
+      e += ((bits[i] >> lane) & 1u) ? -f : f;
     }
-    const int p1 = __ldg(row_ptr + i + 1);
-    for (int p = __ldg(row_ptr + i); p < p1; ++p) {
-      const uint32_t x = bi ^ bits[__ldg(col + p)];
-      const A wt = (A)__ldg(w + p);
+  const int pa = __ldg(row_ptr + r0), pb = __ldg(row_ptr + r1);
+  const int per = (pb - pa + kElocWarps - 1) / kElocWarps;
+  const int p0 = pa + warp * per, p1 = min(pb, p0 + per);
+  for (int pc = p0; pc < p1; pc += 32) {
+    const int p = pc + lane;
+    const bool in = p < p1;
+    const int ei = in ? __ldg(erow + p) : 0, ej = in ? __ldg(col + p) : 0;
+    const A ew = in ? (A)__ldg(w + p) : (A)0;
+    const int cnt = min(32, p1 - pc);
+#pragma unroll 4
+    for (int k = 0; k < cnt; ++k) {
+      const int i = __shfl_sync(0xffffffffu, ei, k), j = __shfl_sync(0xffffffffu, ej, k);
+      const A wt = __shfl_sync(0xffffffffu, ew, k);
+      const uint32_t x = bits[i] ^ bits[j];
       e += ((x >> lane) & 1u) ? -wt : wt;
     }
   }
   red[warp][lane] = e;
   __syncthreads();
+  const int b = 32 * wd + lane;
   if (warp == 0 && b < B) {
     A t = red[0][lane];
 #pragma unroll
-    for (int q = 1; q < kElocWarps; ++q) t += red[q][lane];
-    E[b] = t;
+    for (int k = 1; k < kElocWarps; ++k) t += red[k][lane];
+    part[(size_t)q * ldp + b] = t;
   }
+}
+
+// E_b = sum of the slices' partial energies, in slice order
+template <typename A>
+__global__ void eloc_sum_kernel(int B, int nslices, const A* __restrict__ part, int ldp, A* __restrict__ E) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  A t = part[b];
+  for (int q = 1; q < nslices; ++q) t += part[(size_t)q * ldp + b];
+  E[b] = t;
 }
 
 // E_b = sum over N-tiles of the GEMM's row partials (1/2 s^T J s) + h.s
@@ -165,24 +224,26 @@ __global__ void tile_sum_kernel(int cnt, int ntiles, const float* __restrict__ p
 
 }  // namespace
 
+template <typename W, typename A>
+cudaError_t eloc_sparse(const vqmc_ctx* c, int B, void* d_e, cudaStream_t st) {
+  const size_t smem = (size_t)c->n * sizeof(uint32_t);
+  auto k = eloc_sparse_kernel<W, A>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int ns = c->eloc_slices;
+  A* part = ns > 1 ? (A*)c->eloc_part : (A*)d_e;
+  k<<<dim3((B + 31) / 32, ns), kElocWarps * 32, smem, st>>>(B, c->n, c->Sbits, c->row_ptr, c->erow, c->col,
+                                                           (const W*)c->w, (const W*)c->field, c->eloc_slice, part,
+                                                           c->Bmax);
+  if (ns > 1) eloc_sum_kernel<A><<<(B + 255) / 256, 256, 0, st>>>(B, ns, part, c->Bmax, (A*)d_e);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_eloc_sparse(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
-  const size_t smem = (size_t)c->n * sizeof(uint32_t);
-  const int grid = (B + 31) / 32;
-  if (c->ham == VQMC_HAM_SPARSE_I32) {
-    auto k = eloc_sparse_kernel<int32_t, int32_t>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, kElocWarps * 32, smem, st>>>(B, c->n, d_s, c->row_ptr, c->col, (const int32_t*)c->w,
-                                            (const int32_t*)c->field, (int32_t*)d_e);
-  } else {
-    auto k = eloc_sparse_kernel<float, float>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, kElocWarps * 32, smem, st>>>(B, c->n, d_s, c->row_ptr, c->col, (const float*)c->w,
-                                            (const float*)c->field, (float*)d_e);
-  }
-  return cudaGetLastError();
+  pack_bits_kernel<<<dim3((c->n + 255) / 256, (B + 31) / 32), 256, 0, st>>>(B, c->n, d_s, c->Sbits);
+  return c->ham == VQMC_HAM_SPARSE_I32 ? eloc_sparse<int32_t, int32_t>(c, B, d_e, st)
+                                       : eloc_sparse<float, float>(c, B, d_e, st);
 }
 
 cudaError_t launch_eloc_dense_finish(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st) {

@@ -63,9 +63,8 @@ constexpr int kOffLG = kOffZ + kDmax * kZld * 4;               // logit(u) [D][1
 constexpr int kOffP = kOffLG + kDmax * kS * 4;                 // recent pre-activations [32][16] float
 constexpr int kOffWr = kOffP + kRmax * kS * 4;                 // W1 of recent units [D][32] bf16
 constexpr int kOffVr = kOffWr + kDmax * kRmax * 2;             // W2 of recent units [D][32] bf16
-constexpr int kOffB2 = kOffVr + kDmax * kRmax * 2;             // b2 [D] float
-constexpr int kOffS8 = kOffB2 + kDmax * 4;                     // spins [16][D] int8
-constexpr int kOffBar = kOffS8 + kS * kDmax;                   // mbarriers + slots
+constexpr int kOffSB = kOffVr + kDmax * kRmax * 2;             // drawn spins, bit e%32 of word [16][e/32]
+constexpr int kOffBar = kOffSB + kS * (kDmax / 32) * 4;        // mbarriers + slots
 constexpr int kSmemBytes = 1024 + kOffBar + 256;
 
 struct TcArgs {
@@ -97,6 +96,73 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
   return false;
 }
 
+template <int ACT>
+__device__ __forceinline__ float g1f(float a) {
+  if constexpr (ACT == VQMC_ACT_RELU) return fmaxf(a, 0.0f);
+  else return 1.0f / (1.0f + expf(-a));
+}
+
+// The sequential part of a block: lanes 4s..4s+3 of warps 0-1 draw the spins
+// of sample s; lane 4s+sub carries recent units 8 sub .. 8 sub + 7.  Per
+// step: z = (Z + b2) + sum over recent units of W2 g1 (each g1 recomputed
+// from its pre-activation, rounded to BF16; W2 is zero until the unit is
+// complete), draw, then every recent pre-activation takes W1 s (zero once
+// complete).  Shared-memory operands of step e+1 are loaded during step e.
+template <int ACT>
+__device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf16* Wr, const float* Zs,
+                                      const float* LG, uint32_t* SB, unsigned char* Hs, int s_me, int sub, int klo,
+                                      int R, int steps, bool want_lp, float& lp) {
+  float pre[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) pre[j] = Pr[(8 * sub + j) * kS + s_me];
+  uint4 vv = *reinterpret_cast<const uint4*>(Vr + 8 * sub);
+  uint4 ww = *reinterpret_cast<const uint4*>(Wr + 8 * sub);
+  float zb = Zs[s_me], lg = LG[s_me];
+  uint32_t bits = 0;
+  for (int e = 0; e < steps; ++e) {
+    const int e1 = e + 1 < steps ? e + 1 : e;
+    const uint4 vn = *reinterpret_cast<const uint4*>(Vr + e1 * kRmax + 8 * sub);
+    const uint4 wn = *reinterpret_cast<const uint4*>(Wr + e1 * kRmax + 8 * sub);
+    const float zbn = Zs[e1 * kZld + s_me], lgn = LG[e1 * kS + s_me];
+    const uint32_t vw[4] = {vv.x, vv.y, vv.z, vv.w};
+    float z0 = 0.0f, z1 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      z0 = fmaf(bf_lo(vw[q]), bf16r(g1f<ACT>(pre[2 * q])), z0);
+      z1 = fmaf(bf_hi(vw[q]), bf16r(g1f<ACT>(pre[2 * q + 1])), z1);
+    }
+    float zp = z0 + z1;
+    zp += __shfl_xor_sync(0xffffffffu, zp, 1);
+    zp += __shfl_xor_sync(0xffffffffu, zp, 2);
+    const float z = zb + zp;
+    const bool up = z > lg;  // u < sigma(z)
+    const float sv = up ? 1.0f : -1.0f;
+    const uint32_t wv[4] = {ww.x, ww.y, ww.z, ww.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      pre[2 * q] = fmaf(bf_lo(wv[q]), sv, pre[2 * q]);
+      pre[2 * q + 1] = fmaf(bf_hi(wv[q]), sv, pre[2 * q + 1]);
+    }
+    bits |= (up ? 1u : 0u) << (e & 31);
+    if (want_lp) lp += log_sigmoid(up ? z : -z);
+    if ((e & 31) == 31 || e + 1 == steps) {
+      SB[s_me * (kDmax / 32) + (e >> 5)] = bits;  // the 4 lanes of the sample store the same word
+      bits = 0;
+    }
+    vv = vn, ww = wn, zb = zbn, lg = lgn;
+  }
+  // the recent units are now complete: their g1 joins the GEMM operand
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int r = 8 * sub + j;
+    if (r < R) {
+      const int k = klo + r;
+      *reinterpret_cast<bf16*>(Hs + (k >> 6) * 2048 + sw128_offset(s_me, k & 63)) =
+          __float2bfloat16_rn(g1f<ACT>(pre[j]));
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     sampler_tc_kernel(const __grid_constant__ CUtensorMap mapV, const __grid_constant__ CUtensorMap mapW,
                       const TcArgs g) {
@@ -111,8 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* Pr = reinterpret_cast<float*>(sm + kOffP);
   bf16* Wr = reinterpret_cast<bf16*>(sm + kOffWr);
   bf16* Vr = reinterpret_cast<bf16*>(sm + kOffVr);
-  float* b2s = reinterpret_cast<float*>(sm + kOffB2);
-  int8_t* S8 = reinterpret_cast<int8_t*>(sm + kOffS8);
+  uint32_t* SB = reinterpret_cast<uint32_t*>(sm + kOffSB);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + kOffBar);
   uint64_t* empty = full + kNStage;
   uint64_t* zfull = empty + kNStage;
@@ -256,7 +321,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int R = khi - klo;  // <= kRmax (checked by the host)
       const int steps = min(D, n - b * D);
       // (a) the block's inputs, while the GEMM runs
-      for (int e = tid; e < D; e += 128) b2s[e] = e < steps ? g.b2[b * D + e] : 0.0f;
       for (int q = tid; q < kS * (D / 4); q += 128) {
         const int s = q % kS, t = b * D + 4 * (q / kS);
         const int bb = b0 + s;
@@ -297,8 +361,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const int e = 32 * warp + lane;
         if (e < D) {
+          const float c = e < steps ? __ldg(g.b2 + b * D + e) : 0.0f;
 #pragma unroll
-          for (int q = 0; q < 16; ++q) Zs[e * kZld + q] = v[q];
+          for (int q = 0; q < 16; ++q) Zs[e * kZld + q] = v[q] + c;  // b2 folded in
         }
       }
       if (R > 0 && live) {
@@ -316,53 +381,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("bar.sync 1, 128;" ::: "memory");
       // (c) the D draws of the block (warps 0-1)
       if (warp < 2) {
-        float pre[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) pre[j] = Pr[(8 * sub + j) * kS + s_me];
-        const int act = g.act;
-        for (int e = 0; e < steps; ++e) {
-          const uint4 vv = *reinterpret_cast<const uint4*>(Vr + e * kRmax + 8 * sub);
-          const uint32_t vw[4] = {vv.x, vv.y, vv.z, vv.w};
-          float z0 = 0.0f, z1 = 0.0f;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            z0 = fmaf(bf_lo(vw[q]), bf16r(act_f(act, pre[2 * q])), z0);
-            z1 = fmaf(bf_hi(vw[q]), bf16r(act_f(act, pre[2 * q + 1])), z1);
-          }
-          float zp = z0 + z1;
-          zp += __shfl_xor_sync(0xffffffffu, zp, 1);
-          zp += __shfl_xor_sync(0xffffffffu, zp, 2);
-          const float z = Zs[e * kZld + s_me] + b2s[e] + zp;
-          const bool up = z > LG[e * kS + s_me];  // u < sigma(z)
-          const float sv = up ? 1.0f : -1.0f;
-          const uint4 ww = *reinterpret_cast<const uint4*>(Wr + e * kRmax + 8 * sub);
-          const uint32_t wv[4] = {ww.x, ww.y, ww.z, ww.w};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            pre[2 * q] = fmaf(bf_lo(wv[q]), sv, pre[2 * q]);
-            pre[2 * q + 1] = fmaf(bf_hi(wv[q]), sv, pre[2 * q + 1]);
-          }
-          if (sub == 0) {
-            S8[s_me * kDmax + e] = up ? (int8_t)1 : (int8_t)-1;
-            if (g.logp) lp += log_sigmoid(up ? z : -z);
-          }
-        }
-        // the recent units are now complete: their g1 joins the GEMM operand
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int r = 8 * sub + j;
-          if (r < R) {
-            const int k = klo + r;
-            *reinterpret_cast<bf16*>(Hs + (k >> 6) * 2048 + sw128_offset(s_me, k & 63)) =
-                __float2bfloat16_rn(act_f(act, pre[j]));
-          }
-        }
+        if (g.act == VQMC_ACT_RELU)
+          solve<VQMC_ACT_RELU>(Pr, Vr, Wr, Zs, LG, SB, Hs, s_me, sub, klo, R, steps, g.logp != nullptr, lp);
+        else
+          solve<VQMC_ACT_SIGMOID>(Pr, Vr, Wr, Zs, LG, SB, Hs, s_me, sub, klo, R, steps, g.logp != nullptr, lp);
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
       // (d) spins: GEMM operand for the update, and the output
       for (int q = tid; q < kS * D; q += 128) {
         const int s = q / D, e = q % D;
-        const int8_t y = S8[s * kDmax + e];
+        const int8_t y = (SB[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u ? (int8_t)1 : (int8_t)-1;
         *reinterpret_cast<bf16*>(Ss + (e >> 6) * 2048 + sw128_offset(s, e & 63)) =
             __float2bfloat16_rn(y > 0 ? 1.0f : -1.0f);
         const int bb = b0 + s;

@@ -291,6 +291,31 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
     hsh = fnv1a(hsh, inst->col, (size_t)c->nnz * 4);
     hsh = fnv1a(hsh, inst->w, (size_t)c->nnz * 4);
     if (!ok) return cleanup_fail(VQMC_ERR_CUDA, "copy of the instance failed");
+    // energy kernel: packed spins, and row slices of about equal edge counts so
+    // that (Bmax/32 words) x slices CTAs cover the GPU about twice
+    const int words = (Bmax + 31) / 32;
+    int slices = (2 * c->num_sms + words - 1) / words;
+    slices = slices < 1 ? 1 : (slices > 32 ? 32 : slices);
+    if (slices > n) slices = n;
+    std::vector<int32_t> rb(slices + 1, n);
+    rb[0] = 0;
+    for (int q = 1, i = 0; q < slices; ++q) {
+      const long long target = (long long)c->nnz * q / slices;
+      while (i < n && inst->row_ptr[i] < target) ++i;
+      rb[q] = i;
+    }
+    c->eloc_slices = slices;
+    std::vector<int32_t> er((size_t)c->nnz);
+    for (int i = 0; i < n; ++i)
+      for (int p = inst->row_ptr[i]; p < inst->row_ptr[i + 1]; ++p) er[(size_t)p] = i;
+    VQ_ALLOC(c->erow, (size_t)(c->nnz > 0 ? c->nnz : 1) * 4);
+    if (c->nnz > 0 && cudaMemcpy(c->erow, er.data(), (size_t)c->nnz * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup_fail(VQMC_ERR_CUDA, "copy of the edge rows failed");
+    VQ_ALLOC(c->Sbits, (size_t)words * n * 4);
+    VQ_ALLOC(c->eloc_part, (size_t)slices * Bmax * 4);
+    VQ_ALLOC(c->eloc_slice, (size_t)(slices + 1) * 4);
+    if (cudaMemcpy(c->eloc_slice, rb.data(), (size_t)(slices + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup_fail(VQMC_ERR_CUDA, "copy of the row slices failed");
   }
   if (inst->field) {
     VQ_ALLOC(c->field, (size_t)n * 4);
@@ -315,7 +340,7 @@ void vqmc_destroy(vqmc_ctx* c) {
   void* ptrs[] = {c->theta, c->adam_m, c->adam_v, c->grad, c->wt_s, c->v_s, c->w_s, c->vt_s, c->row_ptr,
                   c->col, c->w, c->field, c->J, c->J_hi, c->J_lo, c->S, c->E, c->Sx, c->St, c->H, c->Ht,
                   c->D, c->Dt, c->GAt, c->logp, c->coef, c->stats, c->row_part, c->col_part, c->err,
-                  c->step_stats};
+                  c->step_stats, c->Sbits, c->eloc_part, c->eloc_slice, c->erow};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -497,9 +522,10 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
   if (h_out) VQ_CUDA(cudaMemcpyAsync(h_out, c->step_stats, sizeof(vqmc_step_stats), cudaMemcpyDeviceToHost, st));
   if (timed) {
     c->timed_steps += 1;
-    // sampler + operand layouts, energy (2 for dense), stats, 7 gradient kernels, Adam + 3 refresh
-    // kernels, stats copy
-    c->launches += 2 + (c->ham == VQMC_HAM_DENSE_F32 ? 2 : 1) + 1 + 7 + 4 + 1;
+    // sampler + operand layouts, energy (dense: GEMM + finish; sparse: pack, slices, slice sum), stats,
+    // 7 gradient kernels, Adam + 3 refresh kernels, stats copy
+    const int energy = c->ham == VQMC_HAM_DENSE_F32 ? 2 : (c->eloc_slices > 1 ? 3 : 2);
+    c->launches += 2 + energy + 1 + 7 + 4 + 1;
   }
   c->iter += 1;
   return VQMC_OK;
