@@ -26,7 +26,7 @@
 //
 // CTA = 16 samples, 6 warps: warps 0-3 own TMEM lanes 32w..32w+31 (read Z
 // and the recent pre-activations, prepare the block's logits and recent
-// weights, write the spins); warps 0-1 are the solver (4 lanes per sample,
+// weights, write the spins); warps 2-3 are the solver (4 lanes per sample,
 // 8 recent units per lane); warp 4 lane 0 streams 128 x 64 BF16 weight tiles
 // with TMA into a 6-stage ring; warp 5 lane 0 issues the MMAs.  Every wait is
 // bounded; after a failed wait the CTA raises the timeout bit and runs on
@@ -58,13 +58,22 @@ constexpr uint32_t kIdesc = idesc_bf16(128, kS);
 constexpr int kOffRing = 0;
 constexpr int kOffH = kOffRing + kNStage * kTileBytes;         // g1, [hp/64] x (16 x 64) swizzled
 constexpr int kOffS = kOffH + (kMaxHp / 64) * 2048;            // spins, [D/64] x (16 x 64) swizzled
-constexpr int kOffZ = kOffS + (kDmax / 64) * 2048;             // Z [D][kZld] float
-constexpr int kOffLG = kOffZ + kDmax * kZld * 4;               // logit(u) [D][16] float
-constexpr int kOffP = kOffLG + kDmax * kS * 4;                 // recent pre-activations [32][16] float
-constexpr int kOffWr = kOffP + kRmax * kS * 4;                 // W1 of recent units [D][32] bf16
-constexpr int kOffVr = kOffWr + kDmax * kRmax * 2;             // W2 of recent units [D][32] bf16
-constexpr int kOffSB = kOffVr + kDmax * kRmax * 2;             // drawn spins, bit e%32 of word [16][e/32]
-constexpr int kOffBar = kOffSB + kS * (kDmax / 32) * 4;        // mbarriers + slots
+// Per-step tables of the solver have kDrows = D + 4 rows (the rows past the
+// block are zero) so that it reads up to 3 steps ahead without clamping.  In
+// the recent-unit tables column kRmax is zero and stands for "no unit".
+constexpr int kDrows = kDmax + 4;
+constexpr int kLdW = kRmax + 8;                                // bf16 row of the recent-unit weight tables
+constexpr int kLdP = kRmax + 4;                                // float row of the per-sample unit tables
+constexpr int kOffZ = kOffS + (kDmax / 64) * 2048;             // Z + b2 [kDrows][kZld] float
+constexpr int kOffLG = kOffZ + kDrows * kZld * 4;              // logit(u) [kDrows][16] float
+constexpr int kOffP = kOffLG + kDrows * kS * 4;                // recent pre-activations at block start [32][16]
+constexpr int kOffWr = kOffP + kRmax * kS * 4;                 // W1 of recent units [kDrows][kLdW] bf16
+constexpr int kOffVr = kOffWr + kDrows * kLdW * 2;             // W2 of recent units [kDrows][kLdW] bf16
+constexpr int kOffPS = kOffVr + kDrows * kLdW * 2;             // solver: current pre-activations [16][kLdP]
+constexpr int kOffHF = kOffPS + kS * kLdP * 4;                 // solver: frozen g1 [16][kLdP]
+constexpr int kOffSB = kOffHF + kS * kLdP * 4;                 // drawn spins, bit e%32 of word [16][e/32]
+constexpr int kOffCU = kOffSB + kS * (kDmax / 32) * 4;         // unit completing at step e-2, [D+5] int
+constexpr int kOffBar = kOffCU + (kDmax + 8) * 4;              // mbarriers + slots
 constexpr int kSmemBytes = 1024 + kOffBar + 256;
 
 struct TcArgs {
@@ -84,12 +93,16 @@ __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__floa
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
-// bounded wait that gives up at once after any failure in the CTA
-__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t* err) {
+// bounded wait that gives up at once after any failure in the CTA; with
+// backoff the polling thread sleeps between tries so that it takes no issue
+// slots from a busy warp on the same sub-partition
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t* err,
+                                              bool backoff = false) {
   if (*abort) return false;
   for (long long it = 0; it < kSpinLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255) == 255 && *abort) return false;
+    if (backoff) __nanosleep(64);
   }
   atomicOr(err, kErrTimeout);
   *abort = 1;
@@ -102,56 +115,115 @@ __device__ __forceinline__ float g1f(float a) {
   else return 1.0f / (1.0f + expf(-a));
 }
 
-// The sequential part of a block: lanes 4s..4s+3 of warps 0-1 draw the spins
-// of sample s; lane 4s+sub carries recent units 8 sub .. 8 sub + 7.  Per
-// step: z = (Z + b2) + sum over recent units of W2 g1 (each g1 recomputed
-// from its pre-activation, rounded to BF16; W2 is zero until the unit is
-// complete), draw, then every recent pre-activation takes W1 s (zero once
-// complete).  Shared-memory operands of step e+1 are loaded during step e.
-template <int ACT>
+// The sequential part of a block: lanes 4s..4s+3 of warps 2-3 draw the spins
+// of sample s; lane 4s+sub owns recent units 8 sub .. 8 sub + 7 (their
+// pre-activations).  With h < n at most one unit completes per step (cu[e]:
+// the unit whose last input is the spin of step e), and
+//     z_e = (Z_e + b2) + sum_{u done by step e-2} W2_eu g1_u    (off the chain)
+//                      + W2_eu1 g1(a_u1 + W1_u1,e-1 s_{e-1})     (u1 = cu[e-1])
+// so the dependence of step e on step e-1 is one FMA, the activation, the
+// BF16 rounding, one FMA and the compare.  The rest of z_{e+2} is assembled
+// two steps ahead: units frozen into hf (done by step e-3; a 4-lane shuffle
+// reduction) plus one explicit term for each later unit.  Every shared-memory
+// operand of step e+1 is loaded during step e, after the lanes have published
+// their pre-activations (for the owner lookup of the next completing unit)
+// and the frozen g1 of the unit done two steps before.  W2_eu is zero for
+// units not yet complete and W1_uj is zero for inputs after a unit's last one,
+// so no masks are needed.
+template <int ACT, bool LP>
 __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf16* Wr, const float* Zs,
-                                      const float* LG, uint32_t* SB, unsigned char* Hs, int s_me, int sub, int klo,
-                                      int R, int steps, bool want_lp, float& lp) {
+                                      const float* LG, const int* CU, uint32_t* SB, float* PreS, float* HfS,
+                                      unsigned char* Hs, int s_me, int sub, int klo, int R, int steps, float& lp) {
   float pre[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) pre[j] = Pr[(8 * sub + j) * kS + s_me];
-  uint4 vv = *reinterpret_cast<const uint4*>(Vr + 8 * sub);
-  uint4 ww = *reinterpret_cast<const uint4*>(Wr + 8 * sub);
-  float zb = Zs[s_me], lg = LG[s_me];
+  float* my_pre = PreS + s_me * kLdP + 8 * sub;
+  const float* my_hf = HfS + s_me * kLdP + 8 * sub;
+  const float* pre_row = PreS + s_me * kLdP;
+  float* hf_row = HfS + s_me * kLdP;
+  reinterpret_cast<float4*>(my_pre)[0] = make_float4(pre[0], pre[1], pre[2], pre[3]);
+  reinterpret_cast<float4*>(my_pre)[1] = make_float4(pre[4], pre[5], pre[6], pre[7]);
+  reinterpret_cast<float4*>(hf_row + 8 * sub)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+  reinterpret_cast<float4*>(hf_row + 8 * sub)[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncwarp();
+  auto wt = [&](int e, int u) { return __bfloat162float(Wr[e * kLdW + u]); };
+  auto vt = [&](int e, int u) { return __bfloat162float(Vr[e * kLdW + u]); };
+  // chain state of step e (cu[-1] = cu[-2] = none)
+  float sv = 0.0f, pc_old = 0.0f, Wc = 0.0f, Vc = 0.0f, h2 = 0.0f;
+  float zbA = Zs[s_me], lg = LG[s_me];
+  float Qp = Zs[kZld + s_me], app = 0.0f;  // z_{e+1} minus the units of steps >= e-1: Qp + app
+  // operands of step e, loaded one step ahead
+  int u0 = CU[2], u1 = kRmax, u2 = kRmax, u0n = CU[3];
+  uint4 wrow = *reinterpret_cast<const uint4*>(Wr + 8 * sub);
+  uint4 vrow = *reinterpret_cast<const uint4*>(Vr + 2 * kLdW + 8 * sub);
+  float4 ha = make_float4(0.f, 0.f, 0.f, 0.f), hb = ha;
+  float Wcn = wt(0, u0), Vcn = vt(1, u0), v1 = 0.0f, v2 = 0.0f, w2 = 0.0f;
+  float zs2 = Zs[2 * kZld + s_me], lgn = LG[kS + s_me], pc_oldn = pre_row[u0];
   uint32_t bits = 0;
+#pragma unroll 2
   for (int e = 0; e < steps; ++e) {
-    const int e1 = e + 1 < steps ? e + 1 : e;
-    const uint4 vn = *reinterpret_cast<const uint4*>(Vr + e1 * kRmax + 8 * sub);
-    const uint4 wn = *reinterpret_cast<const uint4*>(Wr + e1 * kRmax + 8 * sub);
-    const float zbn = Zs[e1 * kZld + s_me], lgn = LG[e1 * kS + s_me];
-    const uint32_t vw[4] = {vv.x, vv.y, vv.z, vv.w};
-    float z0 = 0.0f, z1 = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      z0 = fmaf(bf_lo(vw[q]), bf16r(g1f<ACT>(pre[2 * q])), z0);
-      z1 = fmaf(bf_hi(vw[q]), bf16r(g1f<ACT>(pre[2 * q + 1])), z1);
-    }
-    float zp = z0 + z1;
-    zp += __shfl_xor_sync(0xffffffffu, zp, 1);
-    zp += __shfl_xor_sync(0xffffffffu, zp, 2);
-    const float z = zb + zp;
+    // ---- the chain of step e
+    const float pc = fmaf(Wc, sv, pc_old);
+    const float h1 = bf16r(g1f<ACT>(pc));  // g1 of cu[e-1] (unused when there is none: Vc = 0)
+    const float z = fmaf(Vc, h1, zbA);
     const bool up = z > lg;  // u < sigma(z)
-    const float sv = up ? 1.0f : -1.0f;
-    const uint32_t wv[4] = {ww.x, ww.y, ww.z, ww.w};
+    const float svn = up ? 1.0f : -1.0f;
+    // ---- units frozen by step e-3, at step e+2 (consumed at step e+1)
+    float a0 = 0.0f, a1 = 0.0f;
+    {
+      const uint32_t vw[4] = {vrow.x, vrow.y, vrow.z, vrow.w};
+      a0 = bf_lo(vw[0]) * ha.x;
+      a1 = bf_hi(vw[0]) * ha.y;
+      a0 = fmaf(bf_lo(vw[1]), ha.z, a0);
+      a1 = fmaf(bf_hi(vw[1]), ha.w, a1);
+      a0 = fmaf(bf_lo(vw[2]), hb.x, a0);
+      a1 = fmaf(bf_hi(vw[2]), hb.y, a1);
+      a0 = fmaf(bf_lo(vw[3]), hb.z, a0);
+      a1 = fmaf(bf_hi(vw[3]), hb.w, a1);
+    }
+    float ap = a0 + a1;
+    ap += __shfl_xor_sync(0xffffffffu, ap, 1);
+    ap += __shfl_xor_sync(0xffffffffu, ap, 2);
+    // ---- owned pre-activations take s_e
+    {
+      const uint32_t wv[4] = {wrow.x, wrow.y, wrow.z, wrow.w};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      pre[2 * q] = fmaf(bf_lo(wv[q]), sv, pre[2 * q]);
-      pre[2 * q + 1] = fmaf(bf_hi(wv[q]), sv, pre[2 * q + 1]);
+      for (int q = 0; q < 4; ++q) {
+        pre[2 * q] = fmaf(bf_lo(wv[q]), svn, pre[2 * q]);
+        pre[2 * q + 1] = fmaf(bf_hi(wv[q]), svn, pre[2 * q + 1]);
+      }
     }
-    bits |= (up ? 1u : 0u) << (e & 31);
-    if (want_lp) lp += log_sigmoid(up ? z : -z);
-    if ((e & 31) == 31 || e + 1 == steps) {
-      SB[s_me * (kDmax / 32) + (e >> 5)] = bits;  // the 4 lanes of the sample store the same word
-      bits = 0;
-    }
-    vv = vn, ww = wn, zb = zbn, lg = lgn;
+    // ---- z_{e+1} without its chain term; z_{e+2} without the units of steps >= e
+    zbA = fmaf(v1, h1, Qp + app);
+    Qp = fmaf(v2, h1, fmaf(w2, h2, zs2));
+    app = ap;
+    const uint32_t nb = bits | ((up ? 1u : 0u) << (e & 31));
+    SB[s_me * (kDmax / 32) + (e >> 5)] = nb;  // the 4 lanes of the sample store the same word
+    bits = (e & 31) == 31 ? 0u : nb;
+    if constexpr (LP) lp += log_sigmoid(up ? z : -z);
+    // ---- publish, then load the operands of step e+1
+    __syncwarp();                 // the lanes have read this step's tables
+    hf_row[u2] = h2;              // freeze g1 of cu[e-2] (column kRmax when there is none)
+    reinterpret_cast<float4*>(my_pre)[0] = make_float4(pre[0], pre[1], pre[2], pre[3]);
+    reinterpret_cast<float4*>(my_pre)[1] = make_float4(pre[4], pre[5], pre[6], pre[7]);
+    __syncwarp();
+    const int u0nn = CU[e + 4];
+    wrow = *reinterpret_cast<const uint4*>(Wr + (e + 1) * kLdW + 8 * sub);
+    vrow = *reinterpret_cast<const uint4*>(Vr + (e + 3) * kLdW + 8 * sub);
+    ha = reinterpret_cast<const float4*>(my_hf)[0];
+    hb = reinterpret_cast<const float4*>(my_hf)[1];
+    const float Wcnn = wt(e + 1, u0n), Vcnn = vt(e + 2, u0n);
+    v1 = vt(e + 2, u0);
+    v2 = vt(e + 3, u0);
+    w2 = vt(e + 3, u1);
+    zs2 = Zs[(e + 3) * kZld + s_me];
+    const float lgnn = LG[(e + 2) * kS + s_me];
+    const float pc_oldnn = pre_row[u0n];
+    h2 = h1, sv = svn, pc_old = pc_oldn, Wc = Wcn, Vc = Vcn, lg = lgn;
+    pc_oldn = pc_oldnn, Wcn = Wcnn, Vcn = Vcnn, lgn = lgnn;
+    u2 = u1, u1 = u0, u0 = u0n, u0n = u0nn;
   }
-  // the recent units are now complete: their g1 joins the GEMM operand
+  // every recent unit is complete: its g1 joins the GEMM operand
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int r = 8 * sub + j;
@@ -177,7 +249,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* Pr = reinterpret_cast<float*>(sm + kOffP);
   bf16* Wr = reinterpret_cast<bf16*>(sm + kOffWr);
   bf16* Vr = reinterpret_cast<bf16*>(sm + kOffVr);
+  float* PreS = reinterpret_cast<float*>(sm + kOffPS);
+  float* HfS = reinterpret_cast<float*>(sm + kOffHF);
   uint32_t* SB = reinterpret_cast<uint32_t*>(sm + kOffSB);
+  int* CU = reinterpret_cast<int*>(sm + kOffCU);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + kOffBar);
   uint64_t* empty = full + kNStage;
   uint64_t* zfull = empty + kNStage;
@@ -206,7 +281,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (warp == 5) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
   // g1 of every unit is zero until the unit completes; spins start at zero
-  for (int q = tid; q < (kOffZ - kOffH) / 16; q += kThreads) reinterpret_cast<uint4*>(Hs)[q] = make_uint4(0, 0, 0, 0);
+  // zero g1 (every unit is zero until it completes), the spins, and the
+  // solver tables (their padding rows and "no unit" columns stay zero)
+  for (int q = tid; q < (kOffSB - kOffH) / 16; q += kThreads) reinterpret_cast<uint4*>(Hs)[q] = make_uint4(0, 0, 0, 0);
   fence_proxy_async();
   fence_before();
   __syncthreads();
@@ -233,7 +310,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       int it = 0;
       auto load = [&](const CUtensorMap* map, int x, int y) -> bool {
         const int s = it % kNStage;
-        if (it >= kNStage && !wait_or_abort(smem_u32(&empty[s]), (uint32_t)((it / kNStage - 1) & 1), abort, g.err))
+        if (it >= kNStage &&
+            !wait_or_abort(smem_u32(&empty[s]), (uint32_t)((it / kNStage - 1) & 1), abort, g.err, true))
           return false;
         const uint32_t bar = smem_u32(&full[s]);
         mbar_expect_tx(bar, kTileBytes);
@@ -270,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int klo = count_deg_le(b * D, n, h);
         bool issued = false;
         if (b > 0 && ok) {
-          ok = wait_or_abort(smem_u32(ready), (uint32_t)((b - 1) & 1), abort, g.err);
+          ok = wait_or_abort(smem_u32(ready), (uint32_t)((b - 1) & 1), abort, g.err, true);
           fence_after();
           for (int t = klo / 128; t < ntiles && ok; ++t)
             for (int kk = 0; kk < nkd && ok; ++kk) {
@@ -312,7 +390,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------- warps 0-3: blocks, solver
-    const int s_me = tid >> 2, sub = tid & 3;  // solver lanes (tid < 64)
+    // solver lanes: warps 2-3, on the two SM sub-partitions that do not also
+    // host the producer and MMA warps (warp w runs on sub-partition w % 4)
+    const int s_me = (tid - 64) >> 2, sub = tid & 3;
     float lp = 0.0f;
     const uint32_t tq = tmem + ((uint32_t)(32 * warp) << 16);
     for (int b = 0; b < nblk; ++b) {
@@ -340,10 +420,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int q = tid; q < D * kRmax; q += 128) {
         const int e = q / kRmax, r = q % kRmax;
         const bool in = r < R && e < steps;
-        Vr[q] = in ? g.v[(size_t)(b * D + e) * g.hp + klo + r] : __float2bfloat16_rn(0.0f);  // W2[i0+e][k]
-        Wr[q] = in ? g.wt[(size_t)(i0 + e) * g.hp + klo + r] : __float2bfloat16_rn(0.0f);   // W1[k][i0+e]
+        Vr[e * kLdW + r] = in ? g.v[(size_t)(b * D + e) * g.hp + klo + r] : __float2bfloat16_rn(0.0f);  // W2[i0+e][k]
+        Wr[e * kLdW + r] = in ? g.wt[(size_t)(i0 + e) * g.hp + klo + r] : __float2bfloat16_rn(0.0f);   // W1[k][i0+e]
       }
       for (int q = tid; q < (kRmax - R) * kS; q += 128) Pr[R * kS + q] = 0.0f;
+      for (int e = tid; e < D + 5; e += 128) {  // CU[e] = unit completing at step e - 2
+        const int x = b * D + e - 2;             // its degree would be x + 1
+        int u = kRmax;
+        if (e >= 2 && e - 2 < steps) {
+          const int k = count_deg_le(x + 1, n, h);
+          if (k > count_deg_le(x, n, h)) u = k - 1 - klo;
+        }
+        CU[e] = u;
+      }
       // (b) Z and the recent pre-activations from tensor memory
       const int nc = (klo + 63) / 64;
       wait_or_abort(smem_u32(zfull), (uint32_t)(b & 1), abort, g.err);
@@ -379,12 +468,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       fence_before();
       asm volatile("bar.sync 1, 128;" ::: "memory");
-      // (c) the D draws of the block (warps 0-1)
-      if (warp < 2) {
-        if (g.act == VQMC_ACT_RELU)
-          solve<VQMC_ACT_RELU>(Pr, Vr, Wr, Zs, LG, SB, Hs, s_me, sub, klo, R, steps, g.logp != nullptr, lp);
-        else
-          solve<VQMC_ACT_SIGMOID>(Pr, Vr, Wr, Zs, LG, SB, Hs, s_me, sub, klo, R, steps, g.logp != nullptr, lp);
+      // (c) the D draws of the block (warps 2-3)
+      if (warp >= 2) {
+        const bool relu = g.act == VQMC_ACT_RELU;
+        if (g.logp) {
+          if (relu) solve<VQMC_ACT_RELU, true>(Pr, Vr, Wr, Zs, LG, CU, SB, PreS, HfS, Hs, s_me, sub, klo, R, steps, lp);
+          else solve<VQMC_ACT_SIGMOID, true>(Pr, Vr, Wr, Zs, LG, CU, SB, PreS, HfS, Hs, s_me, sub, klo, R, steps, lp);
+        } else {
+          if (relu) solve<VQMC_ACT_RELU, false>(Pr, Vr, Wr, Zs, LG, CU, SB, PreS, HfS, Hs, s_me, sub, klo, R, steps, lp);
+          else solve<VQMC_ACT_SIGMOID, false>(Pr, Vr, Wr, Zs, LG, CU, SB, PreS, HfS, Hs, s_me, sub, klo, R, steps, lp);
+        }
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
       // (d) spins: GEMM operand for the update, and the output
@@ -400,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       fence_before();
       mbar_arrive(smem_u32(ready));
     }
-    if (tid < 64 && sub == 0 && g.logp && b0 + s_me < g.B && !*abort) g.logp[b0 + s_me] = lp;
+    if (warp >= 2 && sub == 0 && g.logp && b0 + s_me < g.B && !*abort) g.logp[b0 + s_me] = lp;
   }
 
   __syncwarp();
@@ -428,7 +521,8 @@ int max_recent(int n, int h, int D) {
 // does not apply (FP32 weights, more than 2048 hidden units, or more than
 // 32 units completing within every block size).
 int sampler_tc_block(const vqmc_ctx* c) {
-  if (c->prec != VQMC_PREC_BF16 || c->hp > kMaxHp) return 0;
+  // h < n: distinct degrees, at most one unit completes per step
+  if (c->prec != VQMC_PREC_BF16 || c->hp > kMaxHp || c->h >= c->n) return 0;
   for (int D : {128, 64})
     if (max_recent(c->n, c->h, D) <= kRmax) return D;
   return 0;
