@@ -57,24 +57,26 @@ constexpr uint32_t kIdesc = idesc_bf16(128, kS);
 // shared memory map (offsets from a 1024-byte aligned base)
 constexpr int kOffRing = 0;
 constexpr int kOffH = kOffRing + kNStage * kTileBytes;         // g1, [hp/64] x (16 x 64) swizzled
-constexpr int kOffS = kOffH + (kMaxHp / 64) * 2048;            // spins, [D/64] x (16 x 64) swizzled
+constexpr int kOffS = kOffH + (kMaxHp / 64) * 2048;            // spins, [2][D/64] x (16 x 64) swizzled
 // Per-step tables of the solver have kDrows = D + 4 rows (the rows past the
 // block are zero) so that it reads up to 3 steps ahead without clamping.  In
 // the recent-unit tables column kRmax is zero and stands for "no unit".
 constexpr int kDrows = kDmax + 4;
 constexpr int kLdW = kRmax + 8;                                // bf16 row of the recent-unit weight tables
 constexpr int kLdP = kRmax + 4;                                // float row of the per-sample unit tables
-constexpr int kOffZ = kOffS + (kDmax / 64) * 2048;             // Z + b2 [kDrows][kZld] float
-constexpr int kOffLG = kOffZ + kDrows * kZld * 4;              // logit(u) [kDrows][16] float
-constexpr int kOffP = kOffLG + kDrows * kS * 4;                // recent pre-activations at block start [32][16]
+constexpr int kOffHr = kOffS + 2 * (kDmax / 64) * 2048;        // g1 of the last block's recent units, 2 x (16 x 64)
+constexpr int kOffZ = kOffHr + 2 * 2048;                       // Z + b2 [kDrows][kZld] float
+constexpr int kOffLG = kOffZ + kDrows * kZld * 4;              // logit(u) [2][kDrows][16] float
+constexpr int kOffP = kOffLG + 2 * kDrows * kS * 4;            // recent pre-activations at block start [32][16]
 constexpr int kOffWr = kOffP + kRmax * kS * 4;                 // W1 of recent units [kDrows][kLdW] bf16
 constexpr int kOffVr = kOffWr + kDrows * kLdW * 2;             // W2 of recent units [kDrows][kLdW] bf16
 constexpr int kOffPS = kOffVr + kDrows * kLdW * 2;             // solver: current pre-activations [16][kLdP]
 constexpr int kOffHF = kOffPS + kS * kLdP * 4;                 // solver: frozen g1 [16][kLdP]
-constexpr int kOffSB = kOffHF + kS * kLdP * 4;                 // drawn spins, bit e%32 of word [16][e/32]
-constexpr int kOffCU = kOffSB + kS * (kDmax / 32) * 4;         // unit completing at step e-2, [D+5] int
+constexpr int kOffSB = kOffHF + kS * kLdP * 4;                 // drawn spins, bit e%32 of word [2][16][e/32]
+constexpr int kOffCU = kOffSB + 2 * kS * (kDmax / 32) * 4;     // unit completing at step e-2, [D+5] int
 constexpr int kOffBar = kOffCU + (kDmax + 8) * 4;              // mbarriers + slots
-constexpr int kSmemBytes = 1024 + kOffBar + 256;
+constexpr int kSmemBytes = 1024 + kOffBar + 128;
+static_assert(kSmemBytes <= 232448, "shared memory budget");
 
 struct TcArgs {
   int n, h, hp, B, D, act;
@@ -133,7 +135,7 @@ __device__ __forceinline__ float g1f(float a) {
 template <int ACT, bool LP>
 __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf16* Wr, const float* Zs,
                                       const float* LG, const int* CU, uint32_t* SB, float* PreS, float* HfS,
-                                      unsigned char* Hs, int s_me, int sub, int klo, int R, int steps, float& lp) {
+                                      unsigned char* Hr, int s_me, int sub, int klo, int R, int steps, float& lp) {
   float pre[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) pre[j] = Pr[(8 * sub + j) * kS + s_me];
@@ -223,16 +225,44 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
     pc_oldn = pc_oldnn, Wcn = Wcnn, Vcn = Vcnn, lgn = lgnn;
     u2 = u1, u1 = u0, u0 = u0n, u0n = u0nn;
   }
-  // every recent unit is complete: its g1 joins the GEMM operand
+  // every recent unit is complete: its g1 goes to the staging operand Hr
+  // (2 chunks of 64 units from chunk klo / 64)
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int r = 8 * sub + j;
     if (r < R) {
       const int k = klo + r;
-      *reinterpret_cast<bf16*>(Hs + (k >> 6) * 2048 + sw128_offset(s_me, k & 63)) =
+      *reinterpret_cast<bf16*>(Hr + ((k >> 6) - (klo >> 6)) * 2048 + sw128_offset(s_me, k & 63)) =
           __float2bfloat16_rn(g1f<ACT>(pre[j]));
     }
   }
+}
+
+// The schedule of block b, computed alike by the producer, the MMA issuer
+// and the compute warps.  Recent units of block b: [klo, khi).
+struct Blk {
+  int klo, khi;
+  int crit0, crit1;  // update tiles needed before block b's solver (those of its recent units)
+  int bulk0;         // further update tiles [bulk0, ntiles), overlapped with block b's solver
+  int cor0, cor1;    // chunks of block b-1's recent units (Hr), added to Z of block b
+  int np;            // chunks [0, np) of the Z GEMM of block b+1, run during block b's solver
+  bool zinit;        // Z of block b was started during block b-1
+  bool zvalid;       // Z of block b holds any term
+};
+__device__ __forceinline__ Blk blk_of(int b, int n, int h, int D, int ntiles, int nblk) {
+  Blk r;
+  r.klo = count_deg_le(b * D, n, h);
+  r.khi = count_deg_le(b * D + D, n, h);
+  const int kprev = b > 0 ? count_deg_le((b - 1) * D, n, h) : 0;
+  if (b > 0 && r.khi > r.klo) r.crit0 = r.klo / 128, r.crit1 = (r.khi - 1) / 128 + 1;
+  else r.crit0 = r.crit1 = r.klo / 128;
+  r.bulk0 = (b > 0 && b + 1 < nblk) ? (r.crit1 > r.klo / 128 ? r.crit1 : r.klo / 128) : ntiles;
+  if (b > 0 && r.klo > kprev) r.cor0 = kprev / 64, r.cor1 = (r.klo - 1) / 64 + 1;
+  else r.cor0 = r.cor1 = 0;
+  r.np = b + 1 < nblk ? (r.klo + 63) / 64 : 0;
+  r.zinit = b > 0 && (kprev + 63) / 64 > 0;  // np of block b-1
+  r.zvalid = r.zinit || r.cor1 > r.cor0;
+  return r;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -244,6 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* sm = smem_raw + (base - raw);
   unsigned char* Hs = sm + kOffH;
   unsigned char* Ss = sm + kOffS;
+  unsigned char* Hr = sm + kOffHr;
   float* Zs = reinterpret_cast<float*>(sm + kOffZ);
   float* LG = reinterpret_cast<float*>(sm + kOffLG);
   float* Pr = reinterpret_cast<float*>(sm + kOffP);
@@ -257,7 +288,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* empty = full + kNStage;
   uint64_t* zfull = empty + kNStage;
   uint64_t* ready = zfull + 1;
-  uint64_t* drain = ready + 1;
+  uint64_t* merged = ready + 1;
+  uint64_t* drain = merged + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -275,6 +307,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     mbar_init(smem_u32(zfull), 1);
     mbar_init(smem_u32(ready), 128);
+    mbar_init(smem_u32(merged), 128);
     mbar_init(smem_u32(drain), 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -306,6 +339,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 4) {
     // ----------------------------------------------------------- producer
+    // Tiles in the MMA issuer's order; per block b: the update tiles needed
+    // before its solver (W1, block b-1's inputs), the tiles of block b-1's
+    // recent units (W2, block b's rows), the remaining update tiles, then the
+    // Z GEMM of block b+1 over the units complete before block b (W2, block
+    // b+1's rows).
     if (lane == 0) {
       int it = 0;
       auto load = [&](const CUtensorMap* map, int x, int y) -> bool {
@@ -321,12 +359,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       };
       bool ok = true;
       for (int b = 0; b < nblk && ok; ++b) {
-        const int klo = count_deg_le(b * D, n, h);  // units complete before block b
-        if (b > 0)  // W1 tiles for block b-1's inputs, units not yet complete
-          for (int t = klo / 128; t < ntiles && ok; ++t)
-            for (int kk = 0; kk < nkd && ok; ++kk) ok = load(&mapW, (b - 1) * D + 64 * kk, 128 * t);
-        const int nc = (klo + 63) / 64;  // W2 tiles: block rows x complete units
-        for (int c = 0; c < nc && ok; ++c) ok = load(&mapV, 64 * c, b * D);
+        const Blk B = blk_of(b, n, h, D, ntiles, nblk);
+        for (int t = B.crit0; t < B.crit1 && ok; ++t)
+          for (int kk = 0; kk < nkd && ok; ++kk) ok = load(&mapW, (b - 1) * D + 64 * kk, 128 * t);
+        for (int c = B.cor0; c < B.cor1 && ok; ++c) ok = load(&mapV, 64 * c, b * D);
+        for (int t = B.bulk0; t < ntiles && ok; ++t)
+          for (int kk = 0; kk < nkd && ok; ++kk) ok = load(&mapW, (b - 1) * D + 64 * kk, 128 * t);
+        for (int c = 0; c < B.np && ok; ++c) ok = load(&mapV, 64 * c, (b + 1) * D);
       }
       // no copy may still be landing when the CTA exits (after a failure
       // some loaded tiles are never consumed)
@@ -335,54 +374,55 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 5) {
     // --------------------------------------------------------- MMA issuer
+    // Block b: after block b-1's solver, the update of block b's recent units
+    // by block b-1's spins and the terms of block b-1's recent units in Z of
+    // block b (commit -> zfull); then, while block b's solver runs, the rest
+    // of the update and, once block b-1's recent g1 are in the operand, the Z
+    // GEMM of block b+1 into the other Z buffer.
     if (lane == 0) {
       int it = 0;
-      bool ok = true;
+      bool ok = true, any = false;
       auto take = [&]() -> uint32_t {  // next full ring stage (smem address), or 0
         const int s = it % kNStage;
         if (!wait_or_abort(smem_u32(&full[s]), (uint32_t)((it / kNStage) & 1), abort, g.err)) return 0;
         fence_after();
         return base + kOffRing + s * kTileBytes;
       };
+      // one 128 x 64 weight tile against a 16 x 64 operand: 4 MMAs of K = 16
+      auto mma_tile = [&](uint32_t dcol, uint32_t bop, bool acc) -> bool {
+        const uint32_t a = take();
+        if (!a) return false;
+        const uint64_t da = smem_desc_sw128(a), db = smem_desc_sw128(bop);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_bf16(tmem + dcol, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kIdesc, (acc || k > 0) ? 1u : 0u);
+        mma_commit(smem_u32(&empty[it % kNStage]));
+        ++it;
+        any = true;
+        return true;
+      };
       for (int b = 0; b < nblk; ++b) {
-        const int klo = count_deg_le(b * D, n, h);
-        bool issued = false;
+        const Blk B = blk_of(b, n, h, D, ntiles, nblk);
+        const uint32_t s_prev = base + kOffS + ((b - 1) & 1) * (kDmax / 64) * 2048;
         if (b > 0 && ok) {
           ok = wait_or_abort(smem_u32(ready), (uint32_t)((b - 1) & 1), abort, g.err, true);
           fence_after();
-          for (int t = klo / 128; t < ntiles && ok; ++t)
-            for (int kk = 0; kk < nkd && ok; ++kk) {
-              const uint32_t a = take();
-              if (!a) {
-                ok = false;
-                break;
-              }
-              const uint64_t da = smem_desc_sw128(a), db = smem_desc_sw128(base + kOffS + kk * 2048);
-#pragma unroll
-              for (int k = 0; k < 4; ++k)
-                mma_bf16(tmem + (uint32_t)(16 * t), da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kIdesc, 1u);
-              mma_commit(smem_u32(&empty[it % kNStage]));
-              ++it;
-              issued = true;
-            }
         }
-        const int nc = (klo + 63) / 64;
-        for (int c = 0; c < nc && ok; ++c) {
-          const uint32_t a = take();
-          if (!a) {
-            ok = false;
-            break;
-          }
-          const uint64_t da = smem_desc_sw128(a), db = smem_desc_sw128(base + kOffH + c * 2048);
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            mma_bf16(tmem + kZCol, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kIdesc, (c > 0 || k > 0) ? 1u : 0u);
-          mma_commit(smem_u32(&empty[it % kNStage]));
-          ++it;
-          issued = true;
-        }
-        if (ok && issued) mma_commit(smem_u32(zfull));
+        for (int t = B.crit0; t < B.crit1 && ok; ++t)
+          for (int kk = 0; kk < nkd && ok; ++kk) ok = mma_tile((uint32_t)(16 * t), s_prev + kk * 2048, true);
+        const uint32_t zcol = kZCol + 16 * (b & 1);
+        for (int c = B.cor0; c < B.cor1 && ok; ++c)
+          ok = mma_tile(zcol, base + kOffHr + (c - B.cor0) * 2048, B.zinit || c > B.cor0);
+        if (ok && any) mma_commit(smem_u32(zfull));  // also covers the previous block's work
         else mbar_arrive(smem_u32(zfull));
+        for (int t = B.bulk0; t < ntiles && ok; ++t)
+          for (int kk = 0; kk < nkd && ok; ++kk) ok = mma_tile((uint32_t)(16 * t), s_prev + kk * 2048, true);
+        if (B.np > 0 && ok) {
+          ok = wait_or_abort(smem_u32(merged), (uint32_t)(b & 1), abort, g.err, true);
+          fence_after();
+          const uint32_t zn = kZCol + 16 * ((b + 1) & 1);
+          for (int c = 0; c < B.np && ok; ++c) ok = mma_tile(zn, base + kOffH + c * 2048, c > 0);
+        }
       }
       // every MMA has completed before tensor memory is released
       mma_commit(smem_u32(drain));
@@ -390,21 +430,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------- warps 0-3: blocks, solver
-    // solver lanes: warps 2-3, on the two SM sub-partitions that do not also
-    // host the producer and MMA warps (warp w runs on sub-partition w % 4)
+    // Warps 2-3 are the solver (on the two SM sub-partitions that do not
+    // also host the producer and MMA warps: warp w runs on w % 4); warps 0-1
+    // meanwhile prepare the next block's logits and write out the previous
+    // block's spins.
     const int s_me = (tid - 64) >> 2, sub = tid & 3;
     float lp = 0.0f;
     const uint32_t tq = tmem + ((uint32_t)(32 * warp) << 16);
-    for (int b = 0; b < nblk; ++b) {
-      const int i0 = b * D + 1;  // first output (1-based)
-      const int klo = count_deg_le(b * D, n, h), khi = count_deg_le(b * D + D, n, h);
-      const int R = khi - klo;  // <= kRmax (checked by the host)
-      const int steps = min(D, n - b * D);
-      // (a) the block's inputs, while the GEMM runs
-      for (int q = tid; q < kS * (D / 4); q += 128) {
+    // logit(u) of block b's steps into LG buffer b & 1; threads t0, t0 + nt, ...
+    auto logits = [&](int b, int t0, int nt) {
+      float* L = LG + (b & 1) * kDrows * kS;
+      for (int q = t0; q < kS * (D / 4); q += nt) {
         const int s = q % kS, t = b * D + 4 * (q / kS);
         const int bb = b0 + s;
-        float* dst = LG + (size_t)(4 * (q / kS)) * kS + s;
+        float* dst = L + (size_t)(4 * (q / kS)) * kS + s;
         if (g.u) {
 #pragma unroll
           for (int w = 0; w < 4; ++w)
@@ -417,6 +456,28 @@ __global__ void __launch_bounds__(kThreads, 1)
           dst[3 * kS] = logit(to_unit(r.w));
         }
       }
+    };
+    // spins of block b (bits in SB buffer b & 1) to the output; threads t0, t0 + nt, ...
+    auto write_spins = [&](int b, int t0, int nt) {
+      const uint32_t* sb = SB + (b & 1) * kS * (kDmax / 32);
+      const int steps = min(D, n - b * D);
+      for (int q = t0; q < kS * D; q += nt) {
+        const int s = q / D, e = q % D;
+        const int bb = b0 + s;
+        if (bb < g.B && e < steps)
+          g.s_out[(size_t)bb * n + b * D + e] =
+              ((sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u) ? (int8_t)1 : (int8_t)-1;
+      }
+    };
+    logits(0, tid, 128);
+    for (int b = 0; b < nblk; ++b) {
+      const Blk B = blk_of(b, n, h, D, ntiles, nblk);
+      const int i0 = b * D + 1;  // first output (1-based)
+      const int klo = B.klo, khi = B.khi;
+      const int R = khi - klo;  // <= kRmax (checked by the host)
+      const int steps = min(D, n - b * D);
+      // (a) the recent units' weights and completion steps (while the MMAs
+      // of this block's critical part run)
       for (int q = tid; q < D * kRmax; q += 128) {
         const int e = q / kRmax, r = q % kRmax;
         const bool in = r < R && e < steps;
@@ -433,8 +494,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         CU[e] = u;
       }
-      // (b) Z and the recent pre-activations from tensor memory
-      const int nc = (klo + 63) / 64;
+      // (b) Z and the recent pre-activations from tensor memory; block b-1's
+      // recent g1 from the staging operand into the GEMM operand
       wait_or_abort(smem_u32(zfull), (uint32_t)(b & 1), abort, g.err);
       __syncwarp();
       fence_after();
@@ -442,8 +503,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool live = !__any_sync(0xffffffffu, *abort != 0);
       {
         float v[16];
-        if (nc > 0 && live) {
-          tmem_ld16(tq + kZCol, v);
+        if (B.zvalid && live) {
+          tmem_ld16(tq + kZCol + 16 * (b & 1), v);
         } else {
 #pragma unroll
           for (int q = 0; q < 16; ++q) v[q] = 0.0f;
@@ -466,33 +527,54 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-      fence_before();
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      // (c) the D draws of the block (warps 2-3)
-      if (warp >= 2) {
-        const bool relu = g.act == VQMC_ACT_RELU;
-        if (g.logp) {
-          if (relu) solve<VQMC_ACT_RELU, true>(Pr, Vr, Wr, Zs, LG, CU, SB, PreS, HfS, Hs, s_me, sub, klo, R, steps, lp);
-          else solve<VQMC_ACT_SIGMOID, true>(Pr, Vr, Wr, Zs, LG, CU, SB, PreS, HfS, Hs, s_me, sub, klo, R, steps, lp);
-        } else {
-          if (relu) solve<VQMC_ACT_RELU, false>(Pr, Vr, Wr, Zs, LG, CU, SB, PreS, HfS, Hs, s_me, sub, klo, R, steps, lp);
-          else solve<VQMC_ACT_SIGMOID, false>(Pr, Vr, Wr, Zs, LG, CU, SB, PreS, HfS, Hs, s_me, sub, klo, R, steps, lp);
+      if (b > 0) {
+        const int kprev = count_deg_le((b - 1) * D, n, h), cb = kprev >> 6;
+        for (int q = tid; q < (klo - kprev) * kS; q += 128) {
+          const int k = kprev + q / kS, s = q % kS;
+          const uint32_t o = sw128_offset(s, k & 63);
+          bf16* src = reinterpret_cast<bf16*>(Hr + ((k >> 6) - cb) * 2048 + o);
+          *reinterpret_cast<bf16*>(Hs + (k >> 6) * 2048 + o) = *src;
+          *src = __float2bfloat16_rn(0.0f);  // Hr is zero outside the current recent units
         }
       }
+      fence_proxy_async();
+      fence_before();
+      mbar_arrive(smem_u32(merged));
       asm volatile("bar.sync 1, 128;" ::: "memory");
-      // (d) spins: GEMM operand for the update, and the output
-      for (int q = tid; q < kS * D; q += 128) {
-        const int s = q / D, e = q % D;
-        const int8_t y = (SB[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u ? (int8_t)1 : (int8_t)-1;
-        *reinterpret_cast<bf16*>(Ss + (e >> 6) * 2048 + sw128_offset(s, e & 63)) =
-            __float2bfloat16_rn(y > 0 ? 1.0f : -1.0f);
-        const int bb = b0 + s;
-        if (bb < g.B && e < steps) g.s_out[(size_t)bb * n + b * D + e] = y > 0 ? (int8_t)1 : (int8_t)-1;
+      // (c) the D draws of the block (warps 2-3); warps 0-1 meanwhile
+      if (warp >= 2) {
+        const bool relu = g.act == VQMC_ACT_RELU;
+        const float* L = LG + (b & 1) * kDrows * kS;
+        uint32_t* sb = SB + (b & 1) * kS * (kDmax / 32);
+        if (g.logp) {
+          if (relu) solve<VQMC_ACT_RELU, true>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, HfS, Hr, s_me, sub, klo, R, steps, lp);
+          else solve<VQMC_ACT_SIGMOID, true>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, HfS, Hr, s_me, sub, klo, R, steps, lp);
+        } else {
+          if (relu) solve<VQMC_ACT_RELU, false>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, HfS, Hr, s_me, sub, klo, R, steps, lp);
+          else solve<VQMC_ACT_SIGMOID, false>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, HfS, Hr, s_me, sub, klo, R, steps, lp);
+        }
+      } else {
+        if (b + 1 < nblk) logits(b + 1, tid, 64);
+        if (b > 0) write_spins(b - 1, tid, 64);
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      // (d) the block's spins as the update GEMM's operand
+      {
+        const uint32_t* sb = SB + (b & 1) * kS * (kDmax / 32);
+        unsigned char* ss = Ss + (b & 1) * (kDmax / 64) * 2048;
+        for (int q = tid; q < kS * D; q += 128) {
+          const int s = q / D, e = q % D;
+          const bool up = (sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u;
+          *reinterpret_cast<bf16*>(ss + (e >> 6) * 2048 + sw128_offset(s, e & 63)) =
+              __float2bfloat16_rn(up ? 1.0f : -1.0f);
+        }
       }
       fence_proxy_async();
       fence_before();
       mbar_arrive(smem_u32(ready));
     }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    write_spins(nblk - 1, tid, 128);
     if (warp >= 2 && sub == 0 && g.logp && b0 + s_me < g.B && !*abort) g.logp[b0 + s_me] = lp;
   }
 
