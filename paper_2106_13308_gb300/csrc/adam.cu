@@ -60,17 +60,74 @@ __global__ void transpose_kernel(int n, int h, int np, const float* __restrict__
   }
 }
 
-__global__ void adam_kernel(long long d, float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
-                            const float* __restrict__ g, float lr, float b1, float b2, float inv_bc1,
-                            float inv_bc2, float eps) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < d; q += (long long)gridDim.x * blockDim.x) {
-    const float gq = g[q];
-    const float mq = b1 * m[q] + (1.0f - b1) * gq;
-    const float vq = b2 * v[q] + (1.0f - b2) * gq * gq;
-    m[q] = mq;
-    v[q] = vq;
-    theta[q] -= lr * (mq * inv_bc1) / (sqrtf(vq * inv_bc2) + eps);
+// One Adam step on the weight matrices fused with the refresh of their
+// kernel-side copies.  Grid (h/32, n/32, 2): z = 0 for W1^T, z = 1 for W2;
+// each 32 x 32 tile is updated with coalesced accesses along k, written to
+// the row copy (wt_s shifted by one row, v_s), and through shared memory to
+// the transposed copy (w_s, vt_s).  Masked entries have zero gradient and
+// zero moments, so they stay zero.  Padding of the copies is never written
+// (zero since allocation).
+template <typename T>
+__global__ void __launch_bounds__(256) adam_refresh_kernel(int n, int h, int hp, int np, float* __restrict__ theta,
+                                                           float* __restrict__ m, float* __restrict__ v,
+                                                           const float* __restrict__ g, float lr, float b1, float b2,
+                                                           float inv_bc1, float inv_bc2, float eps, T* __restrict__ wt_s,
+                                                           T* __restrict__ v_s, T* __restrict__ w_s,
+                                                           T* __restrict__ vt_s) {
+  __shared__ float tile[32][33];
+  const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32, z = blockIdx.z;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const long long off = z == 0 ? 0 : (long long)n * h + h;
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int r = r0 + rr, k = k0 + tx;
+    if (r < n && k < h) {
+      // theta, the moments and the gradient stream through with the
+      // evict-first policy, so that the weight copies written here (which the
+      // next sampler and GEMMs read) stay in L2
+      const long long q = off + (long long)r * h + k;
+      const float gq = __ldcs(g + q);
+      const float mq = b1 * __ldcs(m + q) + (1.0f - b1) * gq;
+      const float vq = b2 * __ldcs(v + q) + (1.0f - b2) * gq * gq;
+      __stcs(m + q, mq);
+      __stcs(v + q, vq);
+      const float th = __ldcs(theta + q) - lr * (mq * inv_bc1) / (sqrtf(vq * inv_bc2) + eps);
+      __stcs(theta + q, th);
+      if (z == 0) {
+        if (wt_s) wt_s[(long long)(r + 1) * hp + k] = cvt<T>(th);
+      } else {
+        v_s[(long long)r * hp + k] = cvt<T>(th);
+      }
+      tile[rr][tx] = th;
+    }
   }
+  __syncthreads();
+  T* dst = z == 0 ? w_s : vt_s;
+  for (int kk = ty; kk < 32; kk += 8) {
+    const int k = k0 + kk, r = r0 + tx;
+    if (k < h && r < n) dst[(long long)k * np + r] = cvt<T>(tile[tx][kk]);
+  }
+}
+
+// Pulls [p, p + bytes) into L2 (evict-last), one prefetch per 128-byte line.
+__global__ void l2_prefetch_kernel(const char* __restrict__ p, size_t bytes) {
+  for (size_t o = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 128; o < bytes;
+       o += (size_t)gridDim.x * blockDim.x * 128)
+    asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p + o));
+}
+
+// Adam on the biases b1 (after W1^T) and b2 (after W2).
+__global__ void adam_bias_kernel(int n, int h, float* __restrict__ theta, float* __restrict__ m,
+                                 float* __restrict__ v, const float* __restrict__ g, float lr, float b1, float b2,
+                                 float inv_bc1, float inv_bc2, float eps) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= h + n) return;
+  const long long q = t < h ? (long long)n * h + t : 2ll * n * h + h + (t - h);
+  const float gq = g[q];
+  const float mq = b1 * m[q] + (1.0f - b1) * gq;
+  const float vq = b2 * v[q] + (1.0f - b2) * gq * gq;
+  m[q] = mq;
+  v[q] = vq;
+  theta[q] -= lr * (mq * inv_bc1) / (sqrtf(vq * inv_bc2) + eps);
 }
 
 __global__ void split_kernel(int n, int np, const float* __restrict__ J, bf16* __restrict__ hi, bf16* __restrict__ lo) {
@@ -116,11 +173,29 @@ cudaError_t launch_adam(vqmc_ctx* c, const float* d_grad, cudaStream_t st) {
   c->adam_t += 1;
   const double t = (double)c->adam_t;
   const double bc1 = 1.0 - pow((double)c->cfg.beta1, t), bc2 = 1.0 - pow((double)c->cfg.beta2, t);
-  adam_kernel<<<grid_for(c->d), 256, 0, st>>>(c->d, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1,
-                                               c->cfg.beta2, (float)(1.0 / bc1), (float)(1.0 / bc2), c->cfg.eps);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return launch_refresh_weights(c, st);
+  const float ib1 = (float)(1.0 / bc1), ib2 = (float)(1.0 / bc2);
+  const dim3 grid((c->h + 31) / 32, (c->n + 31) / 32, 2), block(32, 8);
+  // the tensor-core sampler reads W1 through w_s; only the CUDA-core one needs wt_s
+  const bool need_wt = c->sampler != VQMC_SAMPLER_TENSOR_CORE;
+  if (c->prec == VQMC_PREC_BF16)
+    adam_refresh_kernel<bf16><<<grid, block, 0, st>>>(
+        c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib1,
+        ib2, c->cfg.eps, need_wt ? (bf16*)c->wt_s : nullptr, (bf16*)c->v_s, (bf16*)c->w_s, (bf16*)c->vt_s);
+  else
+    adam_refresh_kernel<float><<<grid, block, 0, st>>>(
+        c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib1,
+        ib2, c->cfg.eps, need_wt ? (float*)c->wt_s : nullptr, (float*)c->v_s, (float*)c->w_s, (float*)c->vt_s);
+  adam_bias_kernel<<<(c->h + c->n + 255) / 256, 256, 0, st>>>(c->n, c->h, c->theta, c->adam_m, c->adam_v, d_grad,
+                                                              c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib1, ib2,
+                                                              c->cfg.eps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prefetch_sampler_weights(const vqmc_ctx* c, cudaStream_t st) {
+  const size_t es = c->prec == VQMC_PREC_BF16 ? 2 : 4;
+  l2_prefetch_kernel<<<c->num_sms * 4, 256, 0, st>>>((const char*)c->v_s, (size_t)sampler_rows(c->n) * c->hp * es);
+  l2_prefetch_kernel<<<c->num_sms * 4, 256, 0, st>>>((const char*)c->w_s, (size_t)c->h * c->np * es);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_dense_split(vqmc_ctx* c, cudaStream_t st) {

@@ -130,6 +130,8 @@ namespace vqmc {
 cudaError_t launch_uniforms(int B, int n, uint64_t seed, uint64_t iteration, float* d_u, cudaStream_t st);
 cudaError_t launch_sampler(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,
                            float* d_logp, cudaStream_t st);
+// ---- adam.cu: the tensor-core sampler's weight copies (v_s, w_s) into L2
+cudaError_t launch_prefetch_sampler_weights(const vqmc_ctx* c, cudaStream_t st);
 // ---- sampler_tc.cu: block size of the tensor-core sampler for this model, 0
 // if it does not apply; its launcher
 int sampler_tc_block(const vqmc_ctx* c);

@@ -80,7 +80,8 @@ static_assert(kSmemBytes <= 232448, "shared memory budget");
 
 struct TcArgs {
   int n, h, hp, B, D, act;
-  const bf16* wt;     // wt_s [rows][hp]: row j = W1[:, j] (input j)
+  const bf16* w;      // w_s [h][np]: row k = W1[k] (column j-1 = input j)
+  int np;
   const bf16* v;      // v_s  [rows][hp]: row r = W2[r] (output r + 1)
   const float* b1;
   const float* b2;
@@ -478,11 +479,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int steps = min(D, n - b * D);
       // (a) the recent units' weights and completion steps (while the MMAs
       // of this block's critical part run)
-      for (int q = tid; q < D * kRmax; q += 128) {
-        const int e = q / kRmax, r = q % kRmax;
-        const bool in = r < R && e < steps;
-        Vr[e * kLdW + r] = in ? g.v[(size_t)(b * D + e) * g.hp + klo + r] : __float2bfloat16_rn(0.0f);  // W2[i0+e][k]
-        Wr[e * kLdW + r] = in ? g.wt[(size_t)(i0 + e) * g.hp + klo + r] : __float2bfloat16_rn(0.0f);   // W1[k][i0+e]
+      // (all loads of a thread are issued before its stores: the gather is
+      // on the critical path between two solver phases)
+      {
+        const unsigned short* gv = reinterpret_cast<const unsigned short*>(g.v);
+        const unsigned short* gw = reinterpret_cast<const unsigned short*>(g.w);
+        unsigned short* sv = reinterpret_cast<unsigned short*>(Vr);
+        unsigned short* sw = reinterpret_cast<unsigned short*>(Wr);
+        const int nq = D * kRmax / 128;  // 16 or 32 per thread
+        for (int q0 = 0; q0 < nq; q0 += 16) {
+          unsigned short tv[16], tw[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int q = tid + 128 * (q0 + j);
+            const int ev = q / kRmax, rv = q % kRmax;  // W2[i0+ev][klo+rv]
+            tv[j] = (rv < R && ev < steps) ? __ldg(gv + (size_t)(b * D + ev) * g.hp + klo + rv) : (unsigned short)0;
+            const int rw = q / D, ew = q % D;  // W1[klo+rw][i0+ew], contiguous in ew
+            tw[j] = (rw < R && ew < steps) ? __ldg(gw + (size_t)(klo + rw) * g.np + (i0 + ew - 1)) : (unsigned short)0;
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int q = tid + 128 * (q0 + j);
+            sv[(q / kRmax) * kLdW + q % kRmax] = tv[j];
+            sw[(q % D) * kLdW + q / D] = tw[j];
+          }
+        }
       }
       for (int q = tid; q < (kRmax - R) * kS; q += 128) Pr[R * kS + q] = 0.0f;
       for (int e = tid; e < D + 5; e += 128) {  // CU[e] = unit completing at step e - 2
@@ -631,7 +652,8 @@ cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64
   a.B = B;
   a.D = D;
   a.act = c->act;
-  a.wt = reinterpret_cast<const bf16*>(c->wt_s);
+  a.w = reinterpret_cast<const bf16*>(c->w_s);
+  a.np = c->np;
   a.v = reinterpret_cast<const bf16*>(c->v_s);
   a.b1 = c->b1;
   a.b2 = c->b2;

@@ -516,6 +516,9 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
   if (s != VQMC_OK) return s;
   mark(4);
   VQ_CUDA(launch_adam(c, c->grad, st));
+  // the next step's sampler streams v_s and w_s: have them in L2 (the
+  // optimiser's traffic evicted them)
+  if (c->sampler == VQMC_SAMPLER_TENSOR_CORE) VQ_CUDA(launch_prefetch_sampler_weights(c, st));
   mark(5);
   fill_step_stats<<<1, 1, 0, st>>>(c->stats, c->iter, c->err, c->step_stats);
   VQ_CUDA(cudaGetLastError());
@@ -523,9 +526,9 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
   if (timed) {
     c->timed_steps += 1;
     // sampler + operand layouts, energy (dense: GEMM + finish; sparse: pack, slices, slice sum), stats,
-    // 7 gradient kernels, Adam + 3 refresh kernels, stats copy
+    // 7 gradient kernels, Adam with the weight-copy refresh + bias Adam, stats copy
     const int energy = c->ham == VQMC_HAM_DENSE_F32 ? 2 : (c->eloc_slices > 1 ? 3 : 2);
-    c->launches += 2 + energy + 1 + 7 + 4 + 1;
+    c->launches += 2 + energy + 1 + 7 + 2 + (c->sampler == VQMC_SAMPLER_TENSOR_CORE ? 2 : 0) + 1;
   }
   c->iter += 1;
   return VQMC_OK;
