@@ -40,9 +40,6 @@ using namespace tc;
 constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
-__device__ __forceinline__ float log_sigmoidf_(float x) {
-  return x >= 0.0f ? -log1pf(expf(-x)) : x - log1pf(expf(x));
-}
 
 // Sum of v over the 32 lanes for 16 columns by recursive halving: afterwards
 // lane l holds the warp's sum of column colsum16_col(l) (lanes 2c and 2c+1
@@ -78,6 +75,27 @@ __device__ __forceinline__ int colsum16_col(int lane) {
   return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
+// log sigma(x) and sigma(-x) from one exponential: with e = exp(-|x|),
+// log sigma(x) = min(x, 0) - log1p(e) and sigma(-x) = (x >= 0 ? e : 1) / (1 + e).
+__device__ __forceinline__ void logsig_pair(float x, float& ls, float& sm) {
+  const float e = expf(-fabsf(x));
+  ls = fminf(x, 0.0f) - log1pf(e);
+  sm = (x >= 0.0f ? e : 1.0f) / (1.0f + e);
+}
+
+// 16 consecutive BF16 values as two 16-byte stores
+__device__ __forceinline__ void store16_bf16(bf16* dst, const float (&x)[16]) {
+  uint32_t w[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
+    w[q] = *reinterpret_cast<const uint32_t*>(&p);
+  }
+  reinterpret_cast<uint4*>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  reinterpret_cast<uint4*>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+template <int OP>
 __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                                                       const __grid_constant__ CUtensorMap mapB,
                                                       const __grid_constant__ CUtensorMap mapB2, const GemmArgs<bf16> g,
@@ -94,7 +112,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
   float* colbuf = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES + 256);  // [4][BN]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int op = g.op;
+  constexpr int op = OP;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int m1 = min(m0 + BM, g.M), n1 = min(n0 + BN, g.N);
 
@@ -181,50 +199,112 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = 0.0f;
     }
+    const int nb = n0 + c0;                 // first column of the chunk
+    const bool full = mvalid && nb + 16 <= g.N;  // all 16 columns inside
     float cs[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int nn = n0 + c0 + q;
-      const bool in = mvalid && nn < g.N;
-      float colv = 0.0f;
-      if (op == kOpHidden) {
-        if (in) {
-          float x = v[q] + g.bias[nn];
-          x = g.act == VQMC_ACT_RELU ? fmaxf(x, 0.0f) : sigmoidf_(x);
-          const bf16 t = __float2bfloat16_rn(x);
-          g.out[(size_t)m * g.ldo + nn] = t;
-          g.out_t[(size_t)nn * g.ldt + m] = t;
+    for (int q = 0; q < 16; ++q) cs[q] = 0.0f;
+    if constexpr (op == kOpHidden) {
+      float x[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float a = v[q] + (nb + q < g.N ? __ldg(g.bias + nb + q) : 0.0f);
+        x[q] = g.act == VQMC_ACT_RELU ? fmaxf(a, 0.0f) : sigmoidf_(a);
+      }
+      if (full) {
+        store16_bf16(g.out + (size_t)m * g.ldo + nb, x);
+      } else if (mvalid) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (nb + q < g.N) g.out[(size_t)m * g.ldo + nb + q] = __float2bfloat16_rn(x[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (mvalid && nb + q < g.N) g.out_t[(size_t)(nb + q) * g.ldt + m] = __float2bfloat16_rn(x[q]);
+    } else if constexpr (op == kOpOut) {
+      // spins of row m, columns nb..nb+15 (one 16-byte load when aligned)
+      uint32_t neg = 0;  // bit q: spin of column nb + q is -1
+      const int8_t* srow = g.S8 + (size_t)m * g.lds8 + nb;
+      if (full && (reinterpret_cast<uintptr_t>(srow) & 15) == 0) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(srow));
+        const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t sg = (wv[k] >> 7) & 0x01010101u;  // sign bit of each byte
+          neg |= ((sg * 0x01020408u) >> 24 & 0xFu) << (4 * k);
         }
-      } else if (op == kOpOut) {
-        if (in) {
-          const float z = v[q] + g.bias[nn];
-          const float s = g.S8[(size_t)m * g.lds8 + nn] > 0 ? 1.0f : -1.0f;
-          rowsum += log_sigmoidf_(s * z);
-          if (g.coef) {
-            const float d = cm * s * sigmoidf_(-s * z);
-            const bf16 t = __float2bfloat16_rn(d);
-            g.out[(size_t)m * g.ldo + nn] = t;
-            g.out_t[(size_t)nn * g.ldt + m] = t;
-            colv = d;
-          }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (mvalid && nb + q < g.N && srow[q] < 0) neg |= 1u << q;
+      }
+      float d[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const bool in = mvalid && nb + q < g.N;
+        const float z = v[q] + (nb + q < g.N ? __ldg(g.bias + nb + q) : 0.0f);
+        const float sgn = (neg >> q) & 1u ? -1.0f : 1.0f;
+        float ls, sm;
+        logsig_pair(sgn * z, ls, sm);
+        if (in) rowsum += ls;
+        d[q] = in ? cm * sgn * sm : 0.0f;
+        cs[q] = d[q];
+      }
+      if (g.coef) {
+        if (full) {
+          store16_bf16(g.out + (size_t)m * g.ldo + nb, d);
+        } else if (mvalid) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (nb + q < g.N) g.out[(size_t)m * g.ldo + nb + q] = __float2bfloat16_rn(d[q]);
         }
-      } else if (op == kOpGA) {
-        if (in) {
-          const float hv = __bfloat162float(g.aux[(size_t)m * g.ldaux + nn]);
-          const float da = g.act == VQMC_ACT_RELU ? (hv > 0.0f ? 1.0f : 0.0f) : hv * (1.0f - hv);
-          const float x = v[q] * da;
-          g.out_t[(size_t)nn * g.ldt + m] = __float2bfloat16_rn(x);
-          colv = x;
-        }
-      } else if (op == kOpDV || op == kOpDW) {
-        if (in) g.gout[(size_t)m * g.ldg + nn] = gemm_out_kept(op, m, nn, g.n, g.h) ? v[q] : 0.0f;
-      } else if (op == kOpEloc) {
-        if (in) {
-          const float s = g.S8[(size_t)m * g.lds8 + nn] > 0 ? 0.5f : -0.5f;
-          rowsum = fmaf(s, v[q], rowsum);
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (mvalid && nb + q < g.N) g.out_t[(size_t)(nb + q) * g.ldt + m] = __float2bfloat16_rn(d[q]);
+      }
+    } else if constexpr (op == kOpGA) {
+      // the adjoint of the pre-activation: (D V)[m][k] * act'(a), act' from H
+      float hv[16];
+      const bf16* hrow = g.aux + (size_t)m * g.ldaux + nb;
+      if (full) {
+        const uint4 q0 = __ldg(reinterpret_cast<const uint4*>(hrow)), q1 = __ldg(reinterpret_cast<const uint4*>(hrow) + 1);
+        const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) hv[2 * q] = __uint_as_float(w[q] << 16), hv[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) hv[q] = (mvalid && nb + q < g.N) ? __bfloat162float(hrow[q]) : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const bool in = mvalid && nb + q < g.N;
+        const float da = g.act == VQMC_ACT_RELU ? (hv[q] > 0.0f ? 1.0f : 0.0f) : hv[q] * (1.0f - hv[q]);
+        const float x = in ? v[q] * da : 0.0f;
+        if (in) g.out_t[(size_t)(nb + q) * g.ldt + m] = __float2bfloat16_rn(x);
+        cs[q] = x;
+      }
+    } else if constexpr (op == kOpDV || op == kOpDW) {
+      float o[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) o[q] = gemm_out_kept(op, m, nb + q, g.n, g.h) ? v[q] : 0.0f;
+      float* grow = g.gout + (size_t)m * g.ldg + nb;
+      if (full && (reinterpret_cast<uintptr_t>(grow) & 15) == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          reinterpret_cast<float4*>(grow)[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+      } else if (mvalid) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (nb + q < g.N) grow[q] = o[q];
+      }
+    } else if constexpr (op == kOpEloc) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        if (mvalid && nb + q < g.N) {
+          const float sgn = g.S8[(size_t)m * g.lds8 + nb + q] > 0 ? 0.5f : -0.5f;
+          rowsum = fmaf(sgn, v[q], rowsum);
         }
       }
-      cs[q] = colv;
     }
     if (want_col) {
       const float w = colsum16(cs, lane);
@@ -262,9 +342,12 @@ void init_once() {
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   g_have_tc = g_encode != nullptr && major == 10 && minor == 3;
-  if (g_have_tc &&
-      cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
-    g_have_tc = false;
+  const void* kernels[] = {(const void*)gemm_tc_kernel<kOpHidden>, (const void*)gemm_tc_kernel<kOpOut>,
+                           (const void*)gemm_tc_kernel<kOpDV>, (const void*)gemm_tc_kernel<kOpGA>,
+                           (const void*)gemm_tc_kernel<kOpDW>, (const void*)gemm_tc_kernel<kOpEloc>};
+  for (const void* k : kernels)
+    if (g_have_tc && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
+      g_have_tc = false;
 }
 
 bool encode(CUtensorMap* map, const void* ptr, int rows, int cols, int ld) {
@@ -303,7 +386,16 @@ cudaError_t launch_gemm_tc_bf16(const GemmArgs<bf16>& a, cudaStream_t st) {
     mb2 = mb;
   }
   dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM);
-  gemm_tc_kernel<<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, a.Bm2 ? 1 : 0);
+  const int two = a.Bm2 ? 1 : 0;
+  switch (a.op) {
+    case kOpHidden: gemm_tc_kernel<kOpHidden><<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
+    case kOpOut: gemm_tc_kernel<kOpOut><<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
+    case kOpDV: gemm_tc_kernel<kOpDV><<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
+    case kOpGA: gemm_tc_kernel<kOpGA><<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
+    case kOpDW: gemm_tc_kernel<kOpDW><<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
+    case kOpEloc: gemm_tc_kernel<kOpEloc><<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
