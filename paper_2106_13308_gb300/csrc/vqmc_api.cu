@@ -496,10 +496,11 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
     if (ev) cudaEventRecord(ev[part], st);
   };
   mark(0);
-  // (a) exact samples, then their GEMM operand layouts
+  // (a) exact samples
   VQ_CUDA(launch_sampler(c, B, nullptr, c->iter, c->S, nullptr, st));
-  VQ_CUDA(launch_spins_to_operands(c, B, c->S, c->Sx, c->St, st));
   mark(1);
+  // their GEMM operand layouts (timed with the energy part)
+  VQ_CUDA(launch_spins_to_operands(c, B, c->S, c->Sx, c->St, st));
   // (c) local energies
   if (c->ham == VQMC_HAM_DENSE_F32) {
     VQ_CUDA(launch_gemm(c, kOpEloc, B, c->S, nullptr, nullptr, st));
