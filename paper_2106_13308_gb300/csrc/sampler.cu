@@ -1,27 +1,12 @@
-// Persistent autoregressive sampler (Algorithm 1 of the paper, Sec. 2.3) and
-// the Philox4x32-10 uniforms it transforms into exact samples (Sec. 4).
+// Exact autoregressive sampling (Algorithm 1 of the paper, Sec. 2.3) from
+// Philox4x32-10 uniforms (Sec. 4), and the dispatch between the two sampler
+// kernels: the blocked tensor-core sampler (sampler_tc.cu) for the BF16
+// models it covers, the per-step CUDA-core sampler (sampler_impl.cuh,
+// instantiated in sampler_bf16.cu and sampler_f32.cu) for every other model.
 //
-// One CTA owns S = 4*SL samples for all n steps.  Hidden unit k's
-// pre-activation a_k = b1_k + sum_{j <= m(k)} W1_kj s_j lives in registers for
-// every sample of the CTA.  At step i the CTA
-//   (1) adds W1[:, i-1] s_{i-1} to the units with m(k) >= i-1,
-//   (2) applies act() to the units that just became complete (m(k) = i-1),
-//   (3) accumulates z_i = b2_i + sum_{k : m(k) <= i-1} W2_ik act(a_k),
-//   (4) reduces z_i over lanes (shuffles) and warps (shared memory + one
-//       mbarrier phase per step), and every warp then draws
-//       s_i = +1 iff u_{b,i} < sigma(z_i) for all samples of the CTA.
-// Each unit does exactly one multiply-add per step and sample (an update
-// while m(k) >= i, a dot term afterwards), so a sample costs h*n FMA.
-// Rows of W1^T and W2 are streamed into a shared-memory ring by bulk
-// asynchronous copies (cp.async.bulk + mbarrier transaction counts), SPS
-// consecutive rows of each per copy, several stages ahead of use.
-//
-// Lane layout: lane = 8*sg + ug.  The 8 "unit groups" ug of a warp hold 8
-// consecutive hidden units of each slot; the 4 "sample groups" sg hold SL
-// samples each.  Slot r of warp w, lane ug holds unit k = r*8*NW + 8*w + ug.
-// With sorted degrees, at any step every slot of a warp is either a pure dot
-// slot, a pure update slot, or (at most one) mixed slot; a warp-uniform
-// dispatch on the number of pure dot slots selects a fully unrolled body.
+// uniforms_kernel writes the same stream the samplers draw internally:
+// u_{b,i} = word (i mod 4) of Philox4x32-10(counter (i/4, b, iteration),
+// key = seed), as (x >> 8) 2^-24.
 #include <cstdio>
 
 #include "sampler.cuh"
