@@ -473,35 +473,63 @@ __global__ void __launch_bounds__(kThreads, 1)
     logits(0, tid, 128);
     for (int b = 0; b < nblk; ++b) {
       const Blk B = blk_of(b, n, h, D, ntiles, nblk);
-      const int i0 = b * D + 1;  // first output (1-based)
       const int klo = B.klo, khi = B.khi;
       const int R = khi - klo;  // <= kRmax (checked by the host)
       const int steps = min(D, n - b * D);
       // (a) the recent units' weights and completion steps (while the MMAs
       // of this block's critical part run)
-      // (all loads of a thread are issued before its stores: the gather is
-      // on the critical path between two solver phases)
+      // 16-byte global loads, all issued before the shared-memory stores (the
+      // gather sits on the critical path between two solver phases)
       {
-        const unsigned short* gv = reinterpret_cast<const unsigned short*>(g.v);
-        const unsigned short* gw = reinterpret_cast<const unsigned short*>(g.w);
         unsigned short* sv = reinterpret_cast<unsigned short*>(Vr);
         unsigned short* sw = reinterpret_cast<unsigned short*>(Wr);
-        const int nq = D * kRmax / 128;  // 16 or 32 per thread
-        for (int q0 = 0; q0 < nq; q0 += 16) {
-          unsigned short tv[16], tw[16];
+        // W2 rows i0..i0+D-1, units [klo, klo+32): 5 aligned 16-byte pieces per row from unit k8
+        const int k8 = klo & ~7;
+        constexpr int kPV = 5;
+        const int nv = D * kPV;                      // pieces of W2
+        const int nw = kRmax * (D / 8);              // pieces of W1: 32 units x D inputs
+        uint4 pv[5], pw[4];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int q = tid + 128 * (q0 + j);
-            const int ev = q / kRmax, rv = q % kRmax;  // W2[i0+ev][klo+rv]
-            tv[j] = (rv < R && ev < steps) ? __ldg(gv + (size_t)(b * D + ev) * g.hp + klo + rv) : (unsigned short)0;
-            const int rw = q / D, ew = q % D;  // W1[klo+rw][i0+ew], contiguous in ew
-            tw[j] = (rw < R && ew < steps) ? __ldg(gw + (size_t)(klo + rw) * g.np + (i0 + ew - 1)) : (unsigned short)0;
+        for (int j = 0; j < 5; ++j) {
+          const int q = tid + 128 * j;
+          const int e = q / kPV, c = q % kPV;
+          pv[j] = (q < nv && e < steps && k8 + 8 * c < g.hp)
+                      ? __ldg(reinterpret_cast<const uint4*>(g.v + (size_t)(b * D + e) * g.hp + k8) + c)
+                      : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int q = tid + 128 * j;
+          const int r = q / (D / 8), c = q % (D / 8);
+          pw[j] = (q < nw && r < R && 8 * c < steps)  // pieces past the last step stay in [0, np)
+                      ? __ldg(reinterpret_cast<const uint4*>(g.w + (size_t)(klo + r) * g.np + (size_t)b * D) + c)
+                      : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          const int q = tid + 128 * j;
+          if (q < nv) {
+            const int e = q / kPV, c = q % kPV;
+            const uint32_t w[4] = {pv[j].x, pv[j].y, pv[j].z, pv[j].w};
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const int r = k8 + 8 * c + t - klo;  // recent unit index of this element
+              if (r >= 0 && r < kRmax)
+                sv[e * kLdW + r] = (r < R && e < steps) ? (unsigned short)(w[t >> 1] >> (16 * (t & 1))) : (unsigned short)0;
+            }
           }
+        }
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int q = tid + 128 * (q0 + j);
-            sv[(q / kRmax) * kLdW + q % kRmax] = tv[j];
-            sw[(q % D) * kLdW + q / D] = tw[j];
+        for (int j = 0; j < 4; ++j) {
+          const int q = tid + 128 * j;
+          if (q < nw) {
+            const int r = q / (D / 8), c = q % (D / 8);
+            const uint32_t w[4] = {pw[j].x, pw[j].y, pw[j].z, pw[j].w};
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const int e = 8 * c + t;
+              sw[e * kLdW + r] = e < steps ? (unsigned short)(w[t >> 1] >> (16 * (t & 1))) : (unsigned short)0;
+            }
           }
         }
       }
