@@ -108,6 +108,78 @@ __global__ void __launch_bounds__(256) adam_refresh_kernel(int n, int h, int hp,
   }
 }
 
+// The same for h % 4 == 0 with 16-byte accesses: tiles of 32 rows x 128
+// columns, each thread 4 rows x 4 consecutive columns, every load of a thread
+// issued before its arithmetic.
+template <typename T>
+__device__ __forceinline__ void store4(T* p, float a, float b, float c, float d);
+template <>
+__device__ __forceinline__ void store4<float>(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+template <>
+__device__ __forceinline__ void store4<bf16>(bf16* p, float a, float b, float c, float d) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) adam_refresh4_kernel(int n, int h, int hp, int np, float* __restrict__ theta,
+                                                            float* __restrict__ m, float* __restrict__ v,
+                                                            const float* __restrict__ g, float lr, float b1, float b2,
+                                                            float inv_bc1, float inv_bc2, float eps,
+                                                            T* __restrict__ wt_s, T* __restrict__ v_s,
+                                                            T* __restrict__ w_s, T* __restrict__ vt_s) {
+  __shared__ float tile[32][129];
+  const int k0 = blockIdx.x * 128, r0 = blockIdx.y * 32, z = blockIdx.z;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const long long off = z == 0 ? 0 : (long long)n * h + h;
+  const int k = k0 + 4 * tx;
+  float4 G[4], M[4], V[4], TH[4];
+  bool in[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = r0 + ty + 8 * j;
+    in[j] = r < n && k < h;
+    const long long q = off + (long long)r * h + k;
+    if (in[j]) {
+      G[j] = __ldcs(reinterpret_cast<const float4*>(g + q));
+      M[j] = __ldcs(reinterpret_cast<const float4*>(m + q));
+      V[j] = __ldcs(reinterpret_cast<const float4*>(v + q));
+      TH[j] = __ldcs(reinterpret_cast<const float4*>(theta + q));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = r0 + ty + 8 * j, rr = ty + 8 * j;
+    if (!in[j]) continue;
+    const long long q = off + (long long)r * h + k;
+    float gq[4] = {G[j].x, G[j].y, G[j].z, G[j].w}, mq[4] = {M[j].x, M[j].y, M[j].z, M[j].w};
+    float vq[4] = {V[j].x, V[j].y, V[j].z, V[j].w}, th[4] = {TH[j].x, TH[j].y, TH[j].z, TH[j].w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      mq[e] = b1 * mq[e] + (1.0f - b1) * gq[e];
+      vq[e] = b2 * vq[e] + (1.0f - b2) * gq[e] * gq[e];
+      th[e] -= lr * (mq[e] * inv_bc1) / (sqrtf(vq[e] * inv_bc2) + eps);
+      tile[rr][4 * tx + e] = th[e];
+    }
+    __stcs(reinterpret_cast<float4*>(m + q), make_float4(mq[0], mq[1], mq[2], mq[3]));
+    __stcs(reinterpret_cast<float4*>(v + q), make_float4(vq[0], vq[1], vq[2], vq[3]));
+    __stcs(reinterpret_cast<float4*>(theta + q), make_float4(th[0], th[1], th[2], th[3]));
+    if (z == 0) {
+      if (wt_s) store4<T>(wt_s + (long long)(r + 1) * hp + k, th[0], th[1], th[2], th[3]);
+    } else {
+      store4<T>(v_s + (long long)r * hp + k, th[0], th[1], th[2], th[3]);
+    }
+  }
+  __syncthreads();
+  T* dst = z == 0 ? w_s : vt_s;
+  for (int kk = ty; kk < 128; kk += 8) {
+    const int kq = k0 + kk, r = r0 + tx;
+    if (kq < h && r < n) dst[(long long)kq * np + r] = cvt<T>(tile[tx][kk]);
+  }
+}
+
 // Pulls [p, p + bytes) into L2 (evict-last), one prefetch per 128-byte line.
 __global__ void l2_prefetch_kernel(const char* __restrict__ p, size_t bytes) {
   for (size_t o = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 128; o < bytes;
@@ -174,10 +246,19 @@ cudaError_t launch_adam(vqmc_ctx* c, const float* d_grad, cudaStream_t st) {
   const double t = (double)c->adam_t;
   const double bc1 = 1.0 - pow((double)c->cfg.beta1, t), bc2 = 1.0 - pow((double)c->cfg.beta2, t);
   const float ib1 = (float)(1.0 / bc1), ib2 = (float)(1.0 / bc2);
-  const dim3 grid((c->h + 31) / 32, (c->n + 31) / 32, 2), block(32, 8);
+  const bool vec = c->h % 4 == 0;  // rows of theta start on 16-byte boundaries
+  const dim3 grid(vec ? (c->h + 127) / 128 : (c->h + 31) / 32, (c->n + 31) / 32, 2), block(32, 8);
   // the tensor-core sampler reads W1 through w_s; only the CUDA-core one needs wt_s
   const bool need_wt = c->sampler != VQMC_SAMPLER_TENSOR_CORE;
-  if (c->prec == VQMC_PREC_BF16)
+  if (vec && c->prec == VQMC_PREC_BF16)
+    adam_refresh4_kernel<bf16><<<grid, block, 0, st>>>(
+        c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib1,
+        ib2, c->cfg.eps, need_wt ? (bf16*)c->wt_s : nullptr, (bf16*)c->v_s, (bf16*)c->w_s, (bf16*)c->vt_s);
+  else if (vec)
+    adam_refresh4_kernel<float><<<grid, block, 0, st>>>(
+        c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib1,
+        ib2, c->cfg.eps, need_wt ? (float*)c->wt_s : nullptr, (float*)c->v_s, (float*)c->w_s, (float*)c->vt_s);
+  else if (c->prec == VQMC_PREC_BF16)
     adam_refresh_kernel<bf16><<<grid, block, 0, st>>>(
         c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib1,
         ib2, c->cfg.eps, need_wt ? (bf16*)c->wt_s : nullptr, (bf16*)c->v_s, (bf16*)c->w_s, (bf16*)c->vt_s);

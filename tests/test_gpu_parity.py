@@ -308,8 +308,9 @@ def test_logprob_backward_arbitrary_weights_and_autograd():
 
 # -------------------------------------------------------------------- adam
 
-def test_adam_matches_oracle():
-    n, h = 40, 30
+@pytest.mark.parametrize("h", [30, 32])  # scalar path, and the 16-byte path (h % 4 == 0)
+def test_adam_matches_oracle(h):
+    n = 40
     inst = er_instance(n, 0.2, 91)
     theta = inputs.lively_params(n, h, 92)
     m = make_model(n, h, 4, inst, theta=theta)
