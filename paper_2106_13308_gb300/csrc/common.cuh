@@ -135,11 +135,16 @@ cudaError_t launch_prefetch_sampler_weights(const vqmc_ctx* c, cudaStream_t st);
 // ---- sampler_tc.cu: block size of the tensor-core sampler for this model, 0
 // if it does not apply; its launcher
 int sampler_tc_block(const vqmc_ctx* c);
+// sx, stt, sbits: optional copies of the spins for the rest of vqmc_step (the
+// GEMM operands Sx, St and the packed layout of the sparse energy)
 cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,
-                              float* d_logp, cudaStream_t st);
+                              float* d_logp, cudaStream_t st, void* sx = nullptr, void* stt = nullptr,
+                              uint32_t* sbits = nullptr);
 
 // ---- eloc.cu
-cudaError_t launch_eloc_sparse(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st);
+// packed: c->Sbits already holds the spins (written by the sampler)
+cudaError_t launch_eloc_sparse(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st,
+                               bool packed = false);
 cudaError_t launch_eloc_dense_finish(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st);
 cudaError_t launch_stats(const vqmc_ctx* c, int B, const void* d_e, double* d_stats, float* d_coef,
                          cudaStream_t st);

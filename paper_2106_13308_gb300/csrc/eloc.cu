@@ -239,9 +239,10 @@ cudaError_t eloc_sparse(const vqmc_ctx* c, int B, void* d_e, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_eloc_sparse(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st) {
+cudaError_t launch_eloc_sparse(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st,
+                               bool packed) {
   if (B <= 0) return cudaSuccess;
-  pack_bits_kernel<<<dim3((c->n + 255) / 256, (B + 31) / 32), 256, 0, st>>>(B, c->n, d_s, c->Sbits);
+  if (!packed) pack_bits_kernel<<<dim3((c->n + 255) / 256, (B + 31) / 32), 256, 0, st>>>(B, c->n, d_s, c->Sbits);
   return c->ham == VQMC_HAM_SPARSE_I32 ? eloc_sparse<int32_t, int32_t>(c, B, d_e, st)
                                        : eloc_sparse<float, float>(c, B, d_e, st);
 }

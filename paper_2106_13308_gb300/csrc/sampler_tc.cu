@@ -90,6 +90,15 @@ struct TcArgs {
   int8_t* s_out;      // [B][n]
   float* logp;        // [B] or null
   uint32_t* err;
+  // optional copies of the spins for the rest of the step (null when absent):
+  // GEMM operands Sx [B][ldsx] and St [n][ldst] (BF16 +-1) and the packed
+  // layout of the sparse energy, bit l of 32-bit word [w][i] = [s_i of
+  // sample 32 w + l is -1], written as 16-bit halves
+  bf16* sx;
+  int ldsx;
+  bf16* stt;
+  int ldst;
+  uint16_t* sbits;
 };
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -462,13 +471,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto write_spins = [&](int b, int t0, int nt) {
       const uint32_t* sb = SB + (b & 1) * kS * (kDmax / 32);
       const int steps = min(D, n - b * D);
+      const bf16 one = __float2bfloat16_rn(1.0f), mone = __float2bfloat16_rn(-1.0f);
       for (int q = t0; q < kS * D; q += nt) {
         const int s = q / D, e = q % D;
         const int bb = b0 + s;
-        if (bb < g.B && e < steps)
-          g.s_out[(size_t)bb * n + b * D + e] =
-              ((sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u) ? (int8_t)1 : (int8_t)-1;
+        if (bb < g.B && e < steps) {
+          const bool up = (sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u;
+          g.s_out[(size_t)bb * n + b * D + e] = up ? (int8_t)1 : (int8_t)-1;
+          if (g.sx) g.sx[(size_t)bb * g.ldsx + b * D + e] = up ? one : mone;
+        }
       }
+      if (g.stt)
+        for (int q = t0; q < kS * D; q += nt) {
+          const int e = q / kS, s = q % kS;
+          const int bb = b0 + s;
+          if (bb < g.B && e < steps) {
+            const bool up = (sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u;
+            g.stt[(size_t)(b * D + e) * g.ldst + bb] = up ? one : mone;
+          }
+        }
+      if (g.sbits)
+        for (int e = t0; e < steps; e += nt) {
+          uint32_t w = 0;
+#pragma unroll
+          for (int s = 0; s < kS; ++s)
+            if (b0 + s < g.B && !((sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u)) w |= 1u << s;
+          g.sbits[((size_t)(b0 >> 5) * n + b * D + e) * 2 + ((b0 >> 4) & 1)] = (uint16_t)w;
+        }
     };
     logits(0, tid, 128);
     for (int b = 0; b < nblk; ++b) {
@@ -660,7 +689,7 @@ int sampler_tc_block(const vqmc_ctx* c) {
 }
 
 cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,
-                              float* d_logp, cudaStream_t st) {
+                              float* d_logp, cudaStream_t st, void* sx, void* stt, uint32_t* sbits) {
   const int D = sampler_tc_block(c);
   if (D == 0 || !gemm_tc_available()) return cudaErrorNotSupported;
   if (B <= 0) return cudaSuccess;
@@ -693,6 +722,11 @@ cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64
   a.s_out = d_s;
   a.logp = d_logp;
   a.err = c->err;
+  a.sx = reinterpret_cast<bf16*>(sx);
+  a.ldsx = c->np;
+  a.stt = reinterpret_cast<bf16*>(stt);
+  a.ldst = c->Bp;
+  a.sbits = reinterpret_cast<uint16_t*>(sbits);
   sampler_tc_kernel<<<(B + kS - 1) / kS, kThreads, kSmemBytes, st>>>(mapV, mapW, a);
   return cudaGetLastError();
 }

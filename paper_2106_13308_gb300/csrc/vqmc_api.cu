@@ -496,17 +496,21 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
     if (ev) cudaEventRecord(ev[part], st);
   };
   mark(0);
-  // (a) exact samples
-  VQ_CUDA(launch_sampler(c, B, nullptr, c->iter, c->S, nullptr, st));
+  // (a) exact samples; the tensor-core sampler also writes the spins' GEMM
+  // operand layouts and the energy's packed layout, otherwise two kernels
+  // produce them (timed with the energy part)
+  const bool tc = c->sampler == VQMC_SAMPLER_TENSOR_CORE;
+  const bool sparse = c->ham != VQMC_HAM_DENSE_F32;
+  if (tc) VQ_CUDA(launch_sampler_tc(c, B, nullptr, c->iter, c->S, nullptr, st, c->Sx, c->St, sparse ? c->Sbits : nullptr));
+  else VQ_CUDA(launch_sampler(c, B, nullptr, c->iter, c->S, nullptr, st));
   mark(1);
-  // their GEMM operand layouts (timed with the energy part)
-  VQ_CUDA(launch_spins_to_operands(c, B, c->S, c->Sx, c->St, st));
+  if (!tc) VQ_CUDA(launch_spins_to_operands(c, B, c->S, c->Sx, c->St, st));
   // (c) local energies
   if (c->ham == VQMC_HAM_DENSE_F32) {
     VQ_CUDA(launch_gemm(c, kOpEloc, B, c->S, nullptr, nullptr, st));
     VQ_CUDA(launch_eloc_dense_finish(c, B, c->S, c->E, st));
   } else {
-    VQ_CUDA(launch_eloc_sparse(c, B, c->S, c->E, st));
+    VQ_CUDA(launch_eloc_sparse(c, B, c->S, c->E, st, /*packed=*/tc));
   }
   mark(2);
   // (d) FP64 statistics and score-function coefficients
@@ -526,10 +530,12 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
   if (h_out) VQ_CUDA(cudaMemcpyAsync(h_out, c->step_stats, sizeof(vqmc_step_stats), cudaMemcpyDeviceToHost, st));
   if (timed) {
     c->timed_steps += 1;
-    // sampler + operand layouts, energy (dense: GEMM + finish; sparse: pack, slices, slice sum), stats,
-    // 7 gradient kernels, Adam with the weight-copy refresh + bias Adam, stats copy
-    const int energy = c->ham == VQMC_HAM_DENSE_F32 ? 2 : (c->eloc_slices > 1 ? 3 : 2);
-    c->launches += 2 + energy + 1 + 7 + 2 + (c->sampler == VQMC_SAMPLER_TENSOR_CORE ? 2 : 0) + 1;
+    // sampler (+ operand layouts unless the tensor-core sampler writes them), energy (dense: GEMM +
+    // finish; sparse: [pack,] slices [, slice sum]), stats, 7 gradient kernels, Adam with the
+    // weight-copy refresh + bias Adam, [2 L2 prefetches,] step stats
+    const int sampler = tc ? 1 : 2;
+    const int energy = !sparse ? 2 : (tc ? 0 : 1) + 1 + (c->eloc_slices > 1 ? 1 : 0);
+    c->launches += sampler + energy + 1 + 7 + 2 + (tc ? 2 : 0) + 1;
   }
   c->iter += 1;
   return VQMC_OK;
