@@ -156,6 +156,18 @@ def _make(cfg, inst, precision):
     return m
 
 
+def _replica_rate(ms, K, world, device):
+    """Whole-job rate of independent replicas: every rank ran K steps in ms
+    milliseconds; the job's time is the slowest rank's, and the units done are
+    world * K. Returns (max ms over ranks, iterations per second)."""
+    import torch
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * K / (ms / 1000.0)
+
+
 def _timed_steps(m, B, K, W, dist_on):
     """Device time of K steps (CUDA events on the launching stream), after W
     warm-up steps, bracketed by barrier + synchronize; per-part times from the
@@ -320,12 +332,8 @@ def main():
     clocks.start()
     ms, parts, steps, launches = _timed_steps(m, B, K, 0, dist_on)
     clk = clocks.stop()
-    if dist_on:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = _replica_rate(ms, K, world, "cuda")
     ms_per_step = ms / K
-    value = world * K / (ms / 1000.0)
     flags = m.check()
 
     # dominant kernel: the tensor-core sampler, timed alone (the library's
@@ -366,7 +374,10 @@ def main():
                 "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "bf16", "data": "synthetic",
                 "config": _config_json(cfg, inst, world, "BF16 weights, FP32 accumulation and sampler, FP64 stats"),
-                "samples_per_s": value * B, "part_ms": part_ms, "fp32": fp32,
+                "samples_per_s": value * B,
+                # exact samples per second of the sampler alone (uniforms are drawn inside it)
+                "sampler_samples_per_s": world * B / (sample_ms / 1000.0),
+                "part_ms": part_ms, "fp32": fp32,
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clk, "device_error_flags": flags}

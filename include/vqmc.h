@@ -232,6 +232,38 @@ vqmc_status vqmc_adam(vqmc_ctx* ctx, const float* d_grad, vqmc_stream stream);
  * reading; use pinned memory for a truly asynchronous copy). */
 vqmc_status vqmc_step(vqmc_ctx* ctx, int32_t B, vqmc_stream stream, vqmc_step_stats* h_out);
 
+/* A batch of independent problems (each member an ordinary context with its
+ * own model, instance, optimiser and workspaces), stepped together: many
+ * Max-Cut instances of different sizes trained at once, so that small
+ * instances fill the GPU together.  The paper trains one instance at a time
+ * (Sec. 5); this is the same iteration applied to each member. */
+typedef struct vqmc_batch vqmc_batch;
+
+/* Creates `count` >= 1 members, member i from cfgs[i] and insts[i] exactly as
+ * vqmc_create would (same validation and errors; on any error nothing is
+ * kept and *out is untouched), plus up to 8 internal streams.  Synchronous. */
+vqmc_status vqmc_batch_create(const vqmc_config* cfgs, const vqmc_instance* insts, int32_t count,
+                              vqmc_batch** out);
+
+/* Frees the batch and every member.  NULL is accepted. */
+void vqmc_batch_destroy(vqmc_batch* batch);
+
+/* Number of members (0 for NULL). */
+int32_t vqmc_batch_count(const vqmc_batch* batch);
+
+/* Member i, borrowed: usable with every vqmc_* call, valid until
+ * vqmc_batch_destroy, never to be passed to vqmc_destroy.  NULL if i is out
+ * of range. */
+vqmc_ctx* vqmc_batch_member(vqmc_batch* batch, int32_t i);
+
+/* One vqmc_step of every member, member i with B[i] samples (B: `count`
+ * host int32), spread over the internal streams after the work already
+ * queued on `stream`; `stream` then waits for all of them (asynchronous, as
+ * vqmc_step).  h_out: NULL, or `count` records receiving each member's
+ * statistics.  Errors: those of vqmc_step, for the first member that fails
+ * (the members before it have stepped), or INVALID_ARG for a NULL argument. */
+vqmc_status vqmc_batch_step(vqmc_batch* batch, const int32_t* B, vqmc_stream stream, vqmc_step_stats* h_out);
+
 /* Device pointers to the last vqmc_step's samples (int8 [B][n]) and energies
  * (int32/float32 [B]); owned by the context, overwritten by the next step. */
 vqmc_status vqmc_last_batch(vqmc_ctx* ctx, const int8_t** d_s, const void** d_e);
@@ -257,8 +289,8 @@ vqmc_status vqmc_load(vqmc_ctx* ctx, const char* path);
  * number of recorded steps and the number of kernels those steps launched.
  * Enabling resets the record. */
 enum {
-  VQMC_PART_SAMPLE = 0,   /* persistent sampler (uniforms generated in-kernel) */
-  VQMC_PART_ENERGY = 1,   /* local energies */
+  VQMC_PART_SAMPLE = 0,   /* the sampler kernel (uniforms generated in-kernel) */
+  VQMC_PART_ENERGY = 1,   /* local energies (and, after the CUDA-core sampler, the spins' GEMM layouts) */
   VQMC_PART_STATS = 2,    /* FP64 statistics and coefficients */
   VQMC_PART_GRAD = 3,     /* log-prob forward + adjoint GEMMs and reductions */
   VQMC_PART_ADAM = 4,     /* Adam step and weight-copy refresh */

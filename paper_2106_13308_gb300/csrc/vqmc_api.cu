@@ -541,6 +541,92 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
   return VQMC_OK;
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct vqmc_batch {
+  std::vector<vqmc_ctx*> members;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;  // one per internal stream
+  cudaEvent_t fork = nullptr;
+};
+
+namespace {
+
+void batch_free(vqmc_batch* b) {
+  for (vqmc_ctx* c : b->members) vqmc_destroy(c);
+  for (cudaEvent_t e : b->done) cudaEventDestroy(e);
+  for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+vqmc_status vqmc_batch_create(const vqmc_config* cfgs, const vqmc_instance* insts, int32_t count,
+                              vqmc_batch** out) {
+  if (!cfgs || !insts || !out) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  if (count < 1) return fail(VQMC_ERR_INVALID_ARG, "count must be >= 1");
+  vqmc_batch* b = new vqmc_batch();
+  for (int32_t i = 0; i < count; ++i) {
+    vqmc_ctx* c = nullptr;
+    const vqmc_status s = vqmc_create(&cfgs[i], &insts[i], &c);
+    if (s != VQMC_OK) {
+      const std::string msg = std::string("member ") + std::to_string(i) + ": " + vqmc_last_error();
+      batch_free(b);
+      return fail(s, msg);
+    }
+    b->members.push_back(c);
+  }
+  const int k = count < 8 ? count : 8;
+  bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int q = 0; q < k && ok; ++q) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) b->streams.push_back(s);
+    ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) b->done.push_back(e);
+  }
+  if (!ok) {
+    batch_free(b);
+    return fail(VQMC_ERR_CUDA, "could not create the batch's streams");
+  }
+  *out = b;
+  return VQMC_OK;
+}
+
+void vqmc_batch_destroy(vqmc_batch* b) {
+  if (b) batch_free(b);
+}
+
+int32_t vqmc_batch_count(const vqmc_batch* b) { return b ? (int32_t)b->members.size() : 0; }
+
+vqmc_ctx* vqmc_batch_member(vqmc_batch* b, int32_t i) {
+  if (!b || i < 0 || i >= (int32_t)b->members.size()) return nullptr;
+  return b->members[(size_t)i];
+}
+
+vqmc_status vqmc_batch_step(vqmc_batch* b, const int32_t* B, vqmc_stream stream, vqmc_step_stats* h_out) {
+  if (!b || !B) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = S(stream);
+  VQ_CUDA(cudaEventRecord(b->fork, st));
+  const size_t k = b->streams.size();
+  for (size_t q = 0; q < k; ++q) VQ_CUDA(cudaStreamWaitEvent(b->streams[q], b->fork, 0));
+  vqmc_status first = VQMC_OK;
+  for (size_t i = 0; i < b->members.size() && first == VQMC_OK; ++i)
+    first = vqmc_step(b->members[i], B[i], (vqmc_stream)b->streams[i % k], h_out ? &h_out[i] : nullptr);
+  // join every internal stream back into the caller's, also after a failure
+  for (size_t q = 0; q < k; ++q) {
+    VQ_CUDA(cudaEventRecord(b->done[q], b->streams[q]));
+    VQ_CUDA(cudaStreamWaitEvent(st, b->done[q], 0));
+  }
+  return first;
+}
+
 vqmc_status vqmc_timing_enable(vqmc_ctx* c, int enable) {
   if (!c) return fail(VQMC_ERR_INVALID_ARG, "null context");
   if (enable && !c->events) {

@@ -35,7 +35,8 @@ EXPORTS = [
     "vqmc_params_device", "vqmc_params_updated", "vqmc_uniforms", "vqmc_sample", "vqmc_local_energy",
     "vqmc_logprob", "vqmc_logprob_backward", "vqmc_energy_stats", "vqmc_grad", "vqmc_adam", "vqmc_step",
     "vqmc_last_batch", "vqmc_iteration", "vqmc_check", "vqmc_save", "vqmc_load", "vqmc_timing_enable",
-    "vqmc_timing_read", "vqmc_logprob_noalloc", "vqmc_last_error",
+    "vqmc_timing_read", "vqmc_logprob_noalloc", "vqmc_last_error", "vqmc_batch_create", "vqmc_batch_destroy",
+    "vqmc_batch_count", "vqmc_batch_member", "vqmc_batch_step",
 ]
 PARTS = ["sample", "energy", "stats", "grad", "adam"]
 
@@ -104,6 +105,11 @@ def load_library(path: str = LIB_PATH):
         "vqmc_timing_read": (st, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "vqmc_logprob_noalloc": (st, [P, I32, P, P, P]),
         "vqmc_last_error": (ctypes.c_char_p, []),
+        "vqmc_batch_create": (st, [ctypes.POINTER(Config), ctypes.POINTER(Instance), I32, ctypes.POINTER(P)]),
+        "vqmc_batch_destroy": (None, [P]),
+        "vqmc_batch_count": (I32, [P]),
+        "vqmc_batch_member": (P, [P, I32]),
+        "vqmc_batch_step": (st, [P, ctypes.POINTER(I32), P, ctypes.POINTER(StepStats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -246,6 +252,30 @@ class _DeviceArray:
                                          "version": 3, "strides": None}
 
 
+def _describe(n, h, max_batch, instance, act, precision, lr, beta1, beta2, eps, seed, sampler, keep):
+    """The C structures of one problem; keep receives the host arrays they point into."""
+    cfg = Config(int(n), int(h), int(max_batch), ACT[act], PREC[precision], lr, beta1, beta2, eps, SAMPLER[sampler],
+                 int(seed) & (2 ** 64 - 1))
+
+    def arr(a, dt):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.c_void_p)
+
+    kind = instance["kind"]
+    if kind == "dense":
+        inst = Instance(HAM["dense"], int(n), 0, 0, None, None, None, arr(instance.get("field"), np.float32),
+                        arr(instance["J"], np.float32))
+    else:
+        wdt = np.int32 if kind == "sparse_i32" else np.float32
+        inst = Instance(HAM[kind], int(n), int(len(instance["col"])), 0, arr(instance["row_ptr"], np.int32),
+                        arr(instance["col"], np.int32), arr(instance["w"], wdt), arr(instance.get("field"), wdt),
+                        None)
+    return cfg, inst
+
+
 class VQMC:
     """One GPU context: model, instance, optimiser and workspaces.
 
@@ -254,37 +284,26 @@ class VQMC:
     J)."""
 
     def __init__(self, n, h, max_batch, instance, act="relu", precision="bf16", lr=1e-2, beta1=0.9,
-                 beta2=0.999, eps=1e-8, seed=0, sampler="auto"):
+                 beta2=0.999, eps=1e-8, seed=0, sampler="auto", _ctx=None):
         load_library()
         self.n, self.h, self.max_batch = int(n), int(h), int(max_batch)
         self.act, self.precision = act, precision
         self.kind = instance["kind"]
-        cfg = Config(self.n, self.h, self.max_batch, ACT[act], PREC[precision], lr, beta1, beta2, eps,
-                     SAMPLER[sampler], int(seed) & (2 ** 64 - 1))
-        keep = []
-
-        def arr(a, dt):
-            if a is None:
-                return None
-            a = np.ascontiguousarray(a, dtype=dt)
-            keep.append(a)
-            return a.ctypes.data_as(ctypes.c_void_p)
-
-        if self.kind == "dense":
-            inst = Instance(HAM["dense"], self.n, 0, 0, None, None, None,
-                            arr(instance.get("field"), np.float32), arr(instance["J"], np.float32))
-        else:
-            wdt = np.int32 if self.kind == "sparse_i32" else np.float32
-            inst = Instance(HAM[self.kind], self.n, int(len(instance["col"])), 0,
-                            arr(instance["row_ptr"], np.int32), arr(instance["col"], np.int32),
-                            arr(instance["w"], wdt), arr(instance.get("field"), wdt), None)
-        self.ctx = vqmc_create(cfg, inst)
+        self._owned = _ctx is None
+        if _ctx is None:
+            keep = []
+            cfg, inst = _describe(n, h, max_batch, instance, act, precision, lr, beta1, beta2, eps, seed, sampler,
+                                  keep)
+            self.ctx = vqmc_create(cfg, inst)
+        else:  # a member of a VQMCBatch, owned by the batch
+            self.ctx = _ctx
         self.d = vqmc_num_params(self.ctx)
         self.e_dtype = torch.int32 if self.kind == "sparse_i32" else torch.float32
 
     def close(self):
         if getattr(self, "ctx", None):
-            vqmc_destroy(self.ctx)
+            if self._owned:
+                vqmc_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):
@@ -402,3 +421,56 @@ class LogProb(torch.autograd.Function):
         (spins,) = ctx.saved_tensors
         g = ctx.model.logprob_backward(spins, grad_out)
         return g, None, None
+
+
+class VQMCBatch:
+    """Independent problems stepped together (vqmc_batch_*).  ``problems`` is
+    a list of dicts with the keyword arguments of VQMC (n, h, max_batch,
+    instance, and optionally act, precision, lr, beta1, beta2, eps, seed,
+    sampler); ``members[i]`` is a VQMC view of problem i, owned by the batch."""
+
+    def __init__(self, problems):
+        lib = load_library()
+        keep, cfgs, insts = [], [], []
+        defaults = dict(act="relu", precision="bf16", lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, seed=0,
+                        sampler="auto")
+        self.problems = [dict(defaults, **p) for p in problems]
+        for p in self.problems:
+            cfg, inst = _describe(p["n"], p["h"], p["max_batch"], p["instance"], p["act"], p["precision"], p["lr"],
+                                  p["beta1"], p["beta2"], p["eps"], p["seed"], p["sampler"], keep)
+            cfgs.append(cfg)
+            insts.append(inst)
+        count = len(cfgs)
+        ca, ia = (Config * count)(*cfgs), (Instance * count)(*insts)
+        h = ctypes.c_void_p()
+        _check(lib.vqmc_batch_create(ca, ia, count, ctypes.byref(h)))
+        self.handle = h
+        self.members = [VQMC(p["n"], p["h"], p["max_batch"], p["instance"], act=p["act"], precision=p["precision"],
+                             _ctx=ctypes.c_void_p(lib.vqmc_batch_member(h, i))) for i, p in enumerate(self.problems)]
+
+    def __len__(self):
+        return len(self.members)
+
+    def step(self, B, out=None, stream=None):
+        """One iteration of every member, member i with B[i] samples (or B for all)."""
+        count = len(self.members)
+        bs = list(B) if hasattr(B, "__len__") else [int(B)] * count
+        arr = (ctypes.c_int32 * count)(*bs)
+        outp = None
+        if out is not None:
+            assert len(out) == count
+            outp = out
+        _check(_lib.vqmc_batch_step(self.handle, arr, _stream(stream), outp))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for m in self.members:
+                m.ctx = None
+            _lib.vqmc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -102,3 +102,15 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.vqmc_step(None, 1, None, None) == vqmc.VQMC_ERR_INVALID_ARG
     assert lib.vqmc_check(None, None) == vqmc.VQMC_ERR_INVALID_ARG
     lib.vqmc_destroy(None)
+
+
+def test_batch_rejects_bad_arguments(lib):
+    from paper_2106_13308_gb300 import vqmc
+    out = ctypes.c_void_p()
+    cfg = (vqmc.Config * 1)(_cfg(vqmc))
+    inst = (vqmc.Instance * 1)(vqmc.Instance(0, 10, 0, 0, None, None, None, None, None))
+    assert lib.vqmc_batch_create(cfg, inst, 0, ctypes.byref(out)) == vqmc.VQMC_ERR_INVALID_ARG
+    assert lib.vqmc_batch_create(None, inst, 1, ctypes.byref(out)) == vqmc.VQMC_ERR_INVALID_ARG
+    assert lib.vqmc_batch_count(None) == 0
+    assert not lib.vqmc_batch_member(None, 0)
+    assert lib.vqmc_batch_step(None, None, None, None) == vqmc.VQMC_ERR_INVALID_ARG

@@ -170,3 +170,36 @@ def test_full_size_er10000_sampled_outputs(prec):
     g = m.logprob_backward(S, torch.from_numpy(gout).cuda()).cpu().numpy()
     go = oracle.made_to_theta(*oracle.logprob_grad(P, Sn[gsel], gout[gsel].astype(np.float64), code))
     assert rel_err(g, go) <= (1e-4 if prec == "fp32" else 3e-2)
+
+
+@pytest.mark.slow
+def test_bf16_and_fp32_reach_the_same_energy_c3():
+    """Equal-energy check at the benchmark workload: 300 Adam iterations of
+    the BF16 and the plain FP32 model from the same initial parameters and
+    seeds, then the mean energy of 1024 fresh samples, averaged over 3 seeds.
+    The two trajectories differ sample by sample, so the check is
+    statistical: the difference of the seed averages must be within 3
+    standard errors of the seed-to-seed spread, and both runs must have
+    lowered the energy."""
+    cfg = inputs.config("maxcut_er10000")
+    inst = inputs.make_instance(cfg)
+    n, h, B = cfg["n"], cfg["h"], cfg["B"]
+    finals = {"bf16": [], "fp32": []}
+    initial = None
+    for seed in range(3):
+        theta = inputs.made_params(n, h, cfg["param_seed"] + seed, w_std=cfg["w_std"])
+        for prec in ("bf16", "fp32"):
+            m = make_model(n, h, B, inst, precision=prec, theta=theta, seed=100 + seed)
+            if initial is None:
+                S0, _ = m.sample(1024, None, iteration=10**6)
+                initial = m.local_energy(S0).cpu().numpy().astype(np.float64).mean()
+            for _ in range(300):
+                m.step(B)
+            S, _ = m.sample(1024, None, iteration=10**6)
+            finals[prec].append(m.local_energy(S).cpu().numpy().astype(np.float64).mean())
+            assert m.check() == 0
+            del m
+    a, b = np.array(finals["bf16"]), np.array(finals["fp32"])
+    se = np.sqrt(a.var(ddof=1) / len(a) + b.var(ddof=1) / len(b))
+    assert abs(a.mean() - b.mean()) <= 3 * se + 1e-3 * abs(b.mean()), (a, b)
+    assert a.mean() < initial and b.mean() < initial
