@@ -227,7 +227,9 @@ vqmc_status vqmc_adam(vqmc_ctx* ctx, const float* d_grad, vqmc_stream stream);
 /* One full VQMC iteration: sample B configurations with the internal
  * uniforms of the context's iteration counter, local energies, FP64
  * statistics, score-function gradient and one Adam step; then increments the
- * iteration counter.  If h_out is not NULL it receives the step's statistics
+ * iteration counter.  The result equals vqmc_sample + vqmc_local_energy +
+ * vqmc_grad + vqmc_adam; for BF16 the weight-gradient GEMMs apply the Adam
+ * step in their epilogue, so the weight gradient is never stored.  If h_out is not NULL it receives the step's statistics
  * by an asynchronous device-to-host copy on `stream` (synchronise before
  * reading; use pinned memory for a truly asynchronous copy). */
 vqmc_status vqmc_step(vqmc_ctx* ctx, int32_t B, vqmc_stream stream, vqmc_step_stats* h_out);
@@ -292,8 +294,9 @@ enum {
   VQMC_PART_SAMPLE = 0,   /* the sampler kernel (uniforms generated in-kernel) */
   VQMC_PART_ENERGY = 1,   /* local energies (and, after the CUDA-core sampler, the spins' GEMM layouts) */
   VQMC_PART_STATS = 2,    /* FP64 statistics and coefficients */
-  VQMC_PART_GRAD = 3,     /* log-prob forward + adjoint GEMMs and reductions */
-  VQMC_PART_ADAM = 4,     /* Adam step and weight-copy refresh */
+  VQMC_PART_GRAD = 3,     /* log-prob forward + adjoint GEMMs and reductions; for BF16 also the
+                             Adam step on the weights, which the weight-gradient GEMMs apply */
+  VQMC_PART_ADAM = 4,     /* Adam step (BF16: biases only) and weight-copy refresh */
   VQMC_NUM_PARTS = 5
 };
 vqmc_status vqmc_timing_enable(vqmc_ctx* ctx, int enable);

@@ -60,13 +60,33 @@ __global__ void transpose_kernel(int n, int h, int np, const float* __restrict__
   }
 }
 
+// Kept columns [lo, hi) of row r of W1^T (z = 0: r < m(k)) or W2 (z = 1:
+// m(k) <= r); the degrees are sorted, so each row keeps one range.
+__device__ __forceinline__ void kept_range(int z, int r, int n, int h, int* lo, int* hi) {
+  const int c = count_deg_le(r, n, h);  // units with m(k) <= r
+  *lo = z == 0 ? c : 0;
+  *hi = z == 0 ? h : c;
+}
+__device__ __forceinline__ bool kept(int z, int r, int k, int n, int h) {
+  int lo, hi;
+  kept_range(z, r, n, h, &lo, &hi);
+  return k >= lo && k < hi;
+}
+// True if the rows [r0, r0 + nr) x columns [k0, k0 + nk) tile keeps nothing.
+__device__ __forceinline__ bool tile_masked(int z, int r0, int nr, int k0, int nk, int n, int h) {
+  const int r1 = min(r0 + nr, n) - 1, k1 = min(k0 + nk, h) - 1;
+  if (z == 0) return k1 < count_deg_le(r0, n, h);  // the row with the most kept columns
+  return k0 >= count_deg_le(r1, n, h);
+}
+
 // One Adam step on the weight matrices fused with the refresh of their
 // kernel-side copies.  Grid (h/32, n/32, 2): z = 0 for W1^T, z = 1 for W2;
 // each 32 x 32 tile is updated with coalesced accesses along k, written to
 // the row copy (wt_s shifted by one row, v_s), and through shared memory to
-// the transposed copy (w_s, vt_s).  Masked entries have zero gradient and
-// zero moments, so they stay zero.  Padding of the copies is never written
-// (zero since allocation).
+// the transposed copy (w_s, vt_s).  Only entries inside the MADE masks are
+// updated (fully masked tiles return at once), so the masked weights stay
+// zero whatever the gradient holds there.  Padding of the copies is never
+// written (zero since allocation).
 template <typename T>
 __global__ void __launch_bounds__(256) adam_refresh_kernel(int n, int h, int hp, int np, float* __restrict__ theta,
                                                            float* __restrict__ m, float* __restrict__ v,
@@ -77,10 +97,12 @@ __global__ void __launch_bounds__(256) adam_refresh_kernel(int n, int h, int hp,
   __shared__ float tile[32][33];
   const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32, z = blockIdx.z;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  if (tile_masked(z, r0, 32, k0, 32, n, h)) return;
   const long long off = z == 0 ? 0 : (long long)n * h + h;
   for (int rr = ty; rr < 32; rr += 8) {
     const int r = r0 + rr, k = k0 + tx;
-    if (r < n && k < h) {
+    tile[rr][tx] = 0.0f;
+    if (r < n && k < h && kept(z, r, k, n, h)) {
       // theta, the moments and the gradient stream through with the
       // evict-first policy, so that the weight copies written here (which the
       // next sampler and GEMMs read) stay in L2
@@ -104,7 +126,7 @@ __global__ void __launch_bounds__(256) adam_refresh_kernel(int n, int h, int hp,
   T* dst = z == 0 ? w_s : vt_s;
   for (int kk = ty; kk < 32; kk += 8) {
     const int k = k0 + kk, r = r0 + tx;
-    if (k < h && r < n) dst[(long long)k * np + r] = cvt<T>(tile[tx][kk]);
+    if (k < h && r < n && kept(z, r, k, n, h)) dst[(long long)k * np + r] = cvt<T>(tile[tx][kk]);
   }
 }
 
@@ -133,14 +155,17 @@ __global__ void __launch_bounds__(256) adam_refresh4_kernel(int n, int h, int hp
   __shared__ float tile[32][129];
   const int k0 = blockIdx.x * 128, r0 = blockIdx.y * 32, z = blockIdx.z;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  if (tile_masked(z, r0, 32, k0, 128, n, h)) return;
   const long long off = z == 0 ? 0 : (long long)n * h + h;
   const int k = k0 + 4 * tx;
   float4 G[4], M[4], V[4], TH[4];
   bool in[4];
+  int klo[4], khi[4];  // kept columns of row r: [klo, khi)
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int r = r0 + ty + 8 * j;
-    in[j] = r < n && k < h;
+    kept_range(z, r, n, h, &klo[j], &khi[j]);
+    in[j] = r < n && k < h && k + 3 >= klo[j] && k < khi[j];
     const long long q = off + (long long)r * h + k;
     if (in[j]) {
       G[j] = __ldcs(reinterpret_cast<const float4*>(g + q));
@@ -152,12 +177,15 @@ __global__ void __launch_bounds__(256) adam_refresh4_kernel(int n, int h, int hp
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int r = r0 + ty + 8 * j, rr = ty + 8 * j;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) tile[rr][4 * tx + e] = 0.0f;
     if (!in[j]) continue;
     const long long q = off + (long long)r * h + k;
     float gq[4] = {G[j].x, G[j].y, G[j].z, G[j].w}, mq[4] = {M[j].x, M[j].y, M[j].z, M[j].w};
     float vq[4] = {V[j].x, V[j].y, V[j].z, V[j].w}, th[4] = {TH[j].x, TH[j].y, TH[j].z, TH[j].w};
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
+      if (k + e < klo[j] || k + e >= khi[j]) continue;  // masked: stays as it is (zero)
       mq[e] = b1 * mq[e] + (1.0f - b1) * gq[e];
       vq[e] = b2 * vq[e] + (1.0f - b2) * gq[e] * gq[e];
       th[e] -= lr * (mq[e] * inv_bc1) / (sqrtf(vq[e] * inv_bc2) + eps);
@@ -176,7 +204,7 @@ __global__ void __launch_bounds__(256) adam_refresh4_kernel(int n, int h, int hp
   T* dst = z == 0 ? w_s : vt_s;
   for (int kk = ty; kk < 128; kk += 8) {
     const int kq = k0 + kk, r = r0 + tx;
-    if (kq < h && r < n) dst[(long long)kq * np + r] = cvt<T>(tile[tx][kk]);
+    if (kq < h && r < n && kept(z, r, kq, n, h)) dst[(long long)kq * np + r] = cvt<T>(tile[tx][kk]);
   }
 }
 
@@ -241,11 +269,23 @@ cudaError_t launch_refresh_weights(vqmc_ctx* c, cudaStream_t st) {
   return c->prec == VQMC_PREC_BF16 ? refresh<bf16>(c, st) : refresh<float>(c, st);
 }
 
-cudaError_t launch_adam(vqmc_ctx* c, const float* d_grad, cudaStream_t st) {
+AdamStep adam_advance(vqmc_ctx* c) {
   c->adam_t += 1;
   const double t = (double)c->adam_t;
   const double bc1 = 1.0 - pow((double)c->cfg.beta1, t), bc2 = 1.0 - pow((double)c->cfg.beta2, t);
-  const float ib1 = (float)(1.0 / bc1), ib2 = (float)(1.0 / bc2);
+  return AdamStep{(float)(1.0 / bc1), (float)(1.0 / bc2)};
+}
+
+cudaError_t launch_adam_bias(vqmc_ctx* c, const float* d_grad, AdamStep a, cudaStream_t st) {
+  adam_bias_kernel<<<(c->h + c->n + 255) / 256, 256, 0, st>>>(c->n, c->h, c->theta, c->adam_m, c->adam_v, d_grad,
+                                                              c->cfg.lr, c->cfg.beta1, c->cfg.beta2, a.ibc1, a.ibc2,
+                                                              c->cfg.eps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(vqmc_ctx* c, const float* d_grad, cudaStream_t st) {
+  const AdamStep a = adam_advance(c);
+  const float ib1 = a.ibc1, ib2 = a.ibc2;
   const bool vec = c->h % 4 == 0;  // rows of theta start on 16-byte boundaries
   const dim3 grid(vec ? (c->h + 127) / 128 : (c->h + 31) / 32, (c->n + 31) / 32, 2), block(32, 8);
   // the tensor-core sampler reads W1 through w_s; only the CUDA-core one needs wt_s
@@ -266,10 +306,9 @@ cudaError_t launch_adam(vqmc_ctx* c, const float* d_grad, cudaStream_t st) {
     adam_refresh_kernel<float><<<grid, block, 0, st>>>(
         c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib1,
         ib2, c->cfg.eps, need_wt ? (float*)c->wt_s : nullptr, (float*)c->v_s, (float*)c->w_s, (float*)c->vt_s);
-  adam_bias_kernel<<<(c->h + c->n + 255) / 256, 256, 0, st>>>(c->n, c->h, c->theta, c->adam_m, c->adam_v, d_grad,
-                                                              c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib1, ib2,
-                                                              c->cfg.eps);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_adam_bias(c, d_grad, a, st);
 }
 
 cudaError_t launch_prefetch_sampler_weights(const vqmc_ctx* c, cudaStream_t st) {

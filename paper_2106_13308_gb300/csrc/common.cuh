@@ -159,13 +159,18 @@ cudaError_t launch_col_sum(const vqmc_ctx* c, int N, int mtiles, float* out, cud
 enum GemmOp {
   kOpHidden = 0,  // H = act(S W1^T + b1); writes H, Ht
   kOpOut = 1,     // Z = H W2^T + b2; logp row partials; if coef: delta, Dt, dc partials
-  kOpDV = 2,      // dW2 = Dt . Ht^T  (masked) -> grad
+  kOpDV = 2,      // dW2 = Dt . Ht^T  (masked) -> grad, or the Adam step on W2
   kOpGA = 3,      // G = D . W2 ; GA = G * act'(H) -> GAt ; db1 partials
-  kOpDW = 4,      // dW1^T = St . GAt^T (masked) -> grad
+  kOpDW = 4,      // dW1^T = St . GAt^T (masked) -> grad, or the Adam step on W1^T
   kOpEloc = 5     // T = S J (hi/lo) ; row partials 1/2 s.T
 };
+// Adam factors of one step (1 / (1 - beta^t) of both moments) for the
+// weight-gradient GEMMs that apply the step in their epilogue.
+struct AdamStep {
+  float ibc1, ibc2;
+};
 cudaError_t launch_gemm(const vqmc_ctx* c, GemmOp op, int B, const int8_t* d_s, const float* coef,
-                        float* grad, cudaStream_t st);
+                        float* grad, cudaStream_t st, const AdamStep* fuse = nullptr);
 
 // ---- vqmc_api.cu: sets the thread-local message of vqmc_last_error
 vqmc_status set_last_error(vqmc_status s, const std::string& msg);
@@ -177,6 +182,10 @@ size_t noalloc_scratch_bytes(const vqmc_ctx* c, int B);
 cudaError_t launch_mask_params(vqmc_ctx* c, cudaStream_t st);
 cudaError_t launch_refresh_weights(vqmc_ctx* c, cudaStream_t st);
 cudaError_t launch_adam(vqmc_ctx* c, const float* d_grad, cudaStream_t st);
+// advances the step count t; the factors of step t
+AdamStep adam_advance(vqmc_ctx* c);
+// Adam on the biases alone (their gradients in d_grad at theta's layout)
+cudaError_t launch_adam_bias(vqmc_ctx* c, const float* d_grad, AdamStep a, cudaStream_t st);
 cudaError_t launch_dense_split(vqmc_ctx* c, cudaStream_t st);
 
 }  // namespace vqmc

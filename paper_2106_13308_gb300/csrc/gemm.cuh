@@ -42,6 +42,19 @@ struct GemmArgs {
   float* col_part;     // [M-tile][ldc]
   int ldc;
   uint32_t* err;       // device error word (bounded waits)
+  // Adam step fused into the weight-gradient epilogue (tensor-core path,
+  // kOpDV / kOpDW with theta set; gout unused): theta, adam_m and adam_v
+  // point at the weight block, [M][ldg]; the refreshed weights also go to
+  // the transposed copy cp_t[k][m] (row ld_cp_t) and, if set, to the row
+  // copy cp_row[m + cp_shift][k] (row ld_cp_row)
+  float* theta;
+  float* adam_m;
+  float* adam_v;
+  T* cp_t;
+  int ld_cp_t;
+  T* cp_row;
+  int ld_cp_row, cp_shift;
+  float lr, beta1, beta2, ibc1, ibc2, eps;  // ibc = 1 / (1 - beta^t)
 };
 
 // K-range [lo, hi) of the N-tile [n0, n1) (clamped to N) for op.

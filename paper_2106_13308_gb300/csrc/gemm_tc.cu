@@ -4,7 +4,7 @@
 // the log-prob forward (Sec. 2.3), its adjoint (gradient of Sec. 2.1) and the
 // dense local energy.
 //
-// One CTA computes one 128 x 128 output tile with 4 warps:
+// One CTA computes one 128 x 128 output tile with 8 warps:
 //   warp 0 allocates 128 TMEM columns; its lane 0 streams K-tiles of A
 //          (128 x 64) and B (128 x 64) into a 3-stage shared-memory ring with
 //          TMA (cp.async.bulk.tensor, 128-byte swizzle, zero fill beyond the
@@ -12,10 +12,20 @@
 //   warp 1 lane 0 issues tcgen05.mma (M = 128, N = 128, K = 16, four per
 //          K-tile) into the TMEM accumulator and tcgen05.commit-s each stage
 //          back to the producer and, after the last K-tile, to the epilogue;
-//   all 4 warps read the accumulator with tcgen05.ld (warp w owns TMEM lanes
-//          32w..32w+31 = tile rows) and run the op's epilogue.
+//   all 8 warps run the op's epilogue: warp w reads TMEM lanes
+//          32 (w % 4) .. + 31 (its tile rows), columns 64 (w / 4) .. + 63,
+//          with tcgen05.ld.  The epilogue operands that do not depend on the
+//          accumulator (spins, stored activations, bias; the optimiser state
+//          of the fused Adam step) are requested while the main loop runs.
 // With ~100 KB of shared memory two CTAs share an SM, so one CTA's epilogue
 // overlaps the other's main loop.
+//
+// The weight-gradient ops can apply the Adam step (Sec. 5.1) in their
+// epilogue: a CTA holds the complete gradient of its tile (K = all samples),
+// so it updates theta and the moments of the tile's unmasked entries and
+// writes the refreshed BF16 weight copies; the gradient itself is not
+// stored.  Fully masked tiles then do nothing at all: their weights, moments
+// and copies are zero and stay zero.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -28,11 +38,18 @@ namespace vqmc {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64, NSTAGE = 3;
+constexpr int kThreads = 256;
+constexpr int kHalf = BN / 2;  // columns per epilogue thread
 constexpr int TILE_A_BYTES = BM * BK * 2;  // 16 KB
 constexpr int TILE_B_BYTES = BN * BK * 2;  // 16 KB
 constexpr int STAGE_BYTES = TILE_A_BYTES + TILE_B_BYTES;
 constexpr int TMEM_COLS = BN;  // FP32 accumulator: 128 lanes x BN columns
-constexpr int SMEM_BYTES = 1024 /*alignment slack*/ + NSTAGE * STAGE_BYTES + 256 /*barriers*/ + 4 * BN * 4;
+// tiles | barriers (256) | column partials [4][BN] | bias [BN] | row partials [BM]
+constexpr int kOffBars = NSTAGE * STAGE_BYTES;
+constexpr int kOffCol = kOffBars + 256;
+constexpr int kOffBias = kOffCol + 4 * BN * 4;
+constexpr int kOffRow = kOffBias + BN * 4;
+constexpr int SMEM_BYTES = 1024 /*alignment slack*/ + kOffRow + BM * 4;
 
 using namespace tc;
 
@@ -95,33 +112,125 @@ __device__ __forceinline__ void store16_bf16(bf16* dst, const float (&x)[16]) {
   reinterpret_cast<uint4*>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
+// Bits of the 16 spins src[0..15] (bit q set: spin q is -1); columns at or
+// past `valid` read as +1.  One 16-byte load when all 16 are inside and the
+// address is aligned.
+__device__ __forceinline__ uint32_t neg_bits16(const int8_t* src, int valid) {
+  uint32_t neg = 0;
+  if (valid >= 16 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(src));
+    const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t sg = (wv[k] >> 7) & 0x01010101u;  // sign bit of each byte
+      neg |= ((sg * 0x01020408u) >> 24 & 0xFu) << (4 * k);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (q < valid && src[q] < 0) neg |= 1u << q;
+  }
+  return neg;
+}
+
+// Row stride (floats) of a warp's staging block in shared memory: 32 rows x
+// 64 columns, padded so that both row- and column-wise accesses are free of
+// bank conflicts.
+constexpr int kStageLd = kHalf + 1;
+
+// The weight-gradient epilogue of one warp after its 32 x 64 block of the
+// gradient (rows m0w.., columns c0..) was staged in G: row r of the block
+// keeps columns [kl, kh) of lane r's (kl_me, kh_me).  Lanes run along the
+// columns for the row-major arrays (theta, moments, gradient, row copy: one
+// 128-byte line per warp access) and along the rows for the transposed copy.
+// With the fused Adam step, every kept entry gets one Adam update (Sec. 5.1)
+// and the refreshed weight goes to the BF16 copies; otherwise the gradient
+// is stored, zero outside the mask.
+__device__ __forceinline__ void wgrad_block(const GemmArgs<bf16>& g, bool fused, float* G, int m0w, int c0,
+                                            int lane, int kl_me, int kh_me) {
+  for (int r0 = 0; r0 < 32; r0 += 4) {
+    float gq[8], mq[8], vq[8], tq[8];
+    bool keep[8], in[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int r = r0 + (j >> 1), col = lane + 32 * (j & 1);
+      const int kl = __shfl_sync(0xffffffffu, kl_me, r), kh = __shfl_sync(0xffffffffu, kh_me, r);
+      const int m = m0w + r, k = c0 + col;
+      in[j] = m < g.M && k < g.N;
+      keep[j] = in[j] && k >= kl && k < kh;
+      gq[j] = G[r * kStageLd + col];
+      if (fused && keep[j]) {
+        const size_t q = (size_t)m * g.ldg + k;
+        mq[j] = __ldcs(g.adam_m + q);
+        vq[j] = __ldcs(g.adam_v + q);
+        tq[j] = __ldcs(g.theta + q);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int r = r0 + (j >> 1), col = lane + 32 * (j & 1);
+      const int m = m0w + r, k = c0 + col;
+      const size_t q = (size_t)m * g.ldg + k;
+      if (!fused) {
+        if (in[j]) g.gout[q] = keep[j] ? gq[j] : 0.0f;
+        continue;
+      }
+      float t = 0.0f;
+      if (keep[j]) {
+        const float mn = g.beta1 * mq[j] + (1.0f - g.beta1) * gq[j];
+        const float vn = g.beta2 * vq[j] + (1.0f - g.beta2) * gq[j] * gq[j];
+        t = tq[j] - g.lr * (mn * g.ibc1) / (sqrtf(vn * g.ibc2) + g.eps);
+        __stcs(g.adam_m + q, mn);
+        __stcs(g.adam_v + q, vn);
+        __stcs(g.theta + q, t);
+        if (g.cp_row) g.cp_row[(size_t)(m + g.cp_shift) * g.ld_cp_row + k] = __float2bfloat16_rn(t);
+      }
+      G[r * kStageLd + col] = t;
+    }
+  }
+  if (!fused) return;
+  __syncwarp();
+  const int m = m0w + lane;
+  if (m < g.M)
+    for (int col = 0; col < kHalf; ++col) {
+      const int k = c0 + col;
+      if (k >= kl_me && k < kh_me && k < g.N) g.cp_t[(size_t)k * g.ld_cp_t + m] = __float2bfloat16_rn(G[lane * kStageLd + col]);
+    }
+}
+
 template <int OP>
-__global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
-                                                      const __grid_constant__ CUtensorMap mapB,
-                                                      const __grid_constant__ CUtensorMap mapB2, const GemmArgs<bf16> g,
-                                                      int two_pass) {
+__global__ void __launch_bounds__(kThreads, 2) gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                               const __grid_constant__ CUtensorMap mapB,
+                                                               const __grid_constant__ CUtensorMap mapB2,
+                                                               const GemmArgs<bf16> g, int two_pass) {
   uint32_t* err = g.err;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned tiles (128B swizzle atoms)
   unsigned char* smem = smem_raw + (base - raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffBars);
   uint64_t* empty = full + NSTAGE;
   uint64_t* done = empty + NSTAGE;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  float* colbuf = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES + 256);  // [4][BN]
+  float* colbuf = reinterpret_cast<float*>(smem + kOffCol);    // [4][BN]
+  float* bias_s = reinterpret_cast<float*>(smem + kOffBias);   // [BN]
+  float* rowbuf = reinterpret_cast<float*>(smem + kOffRow);    // [BM]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;
   constexpr int op = OP;
+  constexpr bool kWgrad = op == kOpDV || op == kOpDW;
+  const bool fused = kWgrad && g.theta != nullptr;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int m1 = min(m0 + BM, g.M), n1 = min(n0 + BN, g.N);
 
-  // fully masked weight-gradient tiles: zeros, no main loop
-  if ((op == kOpDV || op == kOpDW) && gemm_tile_masked(op, m0, m1, n0, n1, g.n, g.h)) {
-    for (int q = tid; q < BM * BN; q += 128) {
-      const int m = m0 + q / BN, nn = n0 + q % BN;
-      if (m < g.M && nn < g.N) g.gout[(size_t)m * g.ldg + nn] = 0.0f;
-    }
+  // fully masked weight-gradient tiles: zeros (or, with the fused Adam step, nothing)
+  if (kWgrad && gemm_tile_masked(op, m0, m1, n0, n1, g.n, g.h)) {
+    if (!fused)
+      for (int q = tid; q < BM * BN; q += kThreads) {
+        const int m = m0 + q / BN, nn = n0 + q % BN;
+        if (m < g.M && nn < g.N) g.gout[(size_t)m * g.ldg + nn] = 0.0f;
+      }
     return;
   }
   int klo, khi;
@@ -178,28 +287,69 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
   }
   __syncwarp();
 
+  // ------------------------------------ epilogue operands, during the main loop
+  const int m = m0 + quad * 32 + lane;  // this thread's tile row
+  const bool mvalid = m < g.M;
+  const int c0 = n0 + kHalf * half;     // this thread's first column
+  if (tid < BN) bias_s[tid] = ((op == kOpHidden || op == kOpOut) && n0 + tid < g.N) ? g.bias[n0 + tid] : 0.0f;
+  uint32_t neg[kHalf / 16];  // kOpOut / kOpEloc: bit q of neg[c]: spin of column c0 + 16c + q is -1
+  uint4 hpre[kHalf / 8];     // kOpGA: stored activations H[m][c0 .. c0 + 63]
+  if constexpr (op == kOpOut || op == kOpEloc) {
+#pragma unroll
+    for (int c = 0; c < kHalf / 16; ++c)
+      neg[c] = mvalid ? neg_bits16(g.S8 + (size_t)m * g.lds8 + c0 + 16 * c, g.N - (c0 + 16 * c)) : 0u;
+  }
+  if constexpr (op == kOpGA) {
+    const bf16* hrow = g.aux + (size_t)m * g.ldaux + c0;
+    const bool vec = mvalid && c0 + kHalf <= g.N && (reinterpret_cast<uintptr_t>(hrow) & 15) == 0;
+#pragma unroll
+    for (int c = 0; c < kHalf / 8; ++c) {
+      if (vec) {
+        hpre[c] = __ldg(reinterpret_cast<const uint4*>(hrow) + c);
+      } else {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int k0 = c0 + 8 * c + 2 * q;
+          const uint32_t lo = (mvalid && k0 < g.N) ? (uint32_t)__bfloat16_as_ushort(hrow[8 * c + 2 * q]) : 0u;
+          const uint32_t hi = (mvalid && k0 + 1 < g.N) ? (uint32_t)__bfloat16_as_ushort(hrow[8 * c + 2 * q + 1]) : 0u;
+          w[q] = lo | (hi << 16);
+        }
+        hpre[c] = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+  }
+  // kept columns of row m in a weight-gradient block: [kl, kh)
+  int kl = 0, kh = g.N;
+  if constexpr (kWgrad) {
+    const int cd = count_deg_le(m, g.n, g.h);  // units with m(k) <= m
+    if (op == kOpDV) kh = min(cd, g.N);         // W2[m][k] needs m(k) <= m
+    else kl = cd;                               // W1^T[m][k] needs m < m(k)
+  }
+
   // ----------------------------------------------------------- epilogue
   const bool done_ok = mbar_wait(smem_u32(done), 0u, err);
   __syncwarp();
   fence_after();
-  const int m = m0 + warp * 32 + lane;  // this thread's tile row
-  const bool mvalid = m < g.M;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  __syncthreads();  // bias_s
+  const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(kHalf * half);
   // warp-uniform: tcgen05.ld is executed by all lanes of a warp or none
   const bool acc_valid = __all_sync(0xffffffffu, nkt > 0 && done_ok);
   float rowsum = 0.0f;
   const bool want_col = g.col_part && ((op == kOpOut && g.coef) || op == kOpGA);
   const float cm = (op == kOpOut && g.coef && mvalid) ? g.coef[m] : 0.0f;
 
-  for (int c0 = 0; c0 < BN; c0 += 16) {
+#pragma unroll
+  for (int c = 0; c < kHalf / 16; ++c) {
     float v[16];
     if (acc_valid) {
-      tmem_ld16(trow + (uint32_t)c0, v);
+      tmem_ld16(trow + (uint32_t)(16 * c), v);
     } else {
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = 0.0f;
     }
-    const int nb = n0 + c0;                 // first column of the chunk
+    const int nb = c0 + 16 * c;                  // first column of the chunk
+    const int lb = nb - n0;                      // its column inside the tile
     const bool full = mvalid && nb + 16 <= g.N;  // all 16 columns inside
     float cs[16];
 #pragma unroll
@@ -208,7 +358,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
       float x[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const float a = v[q] + (nb + q < g.N ? __ldg(g.bias + nb + q) : 0.0f);
+        const float a = v[q] + bias_s[lb + q];
         x[q] = g.act == VQMC_ACT_RELU ? fmaxf(a, 0.0f) : sigmoidf_(a);
       }
       if (full) {
@@ -222,28 +372,12 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
       for (int q = 0; q < 16; ++q)
         if (mvalid && nb + q < g.N) g.out_t[(size_t)(nb + q) * g.ldt + m] = __float2bfloat16_rn(x[q]);
     } else if constexpr (op == kOpOut) {
-      // spins of row m, columns nb..nb+15 (one 16-byte load when aligned)
-      uint32_t neg = 0;  // bit q: spin of column nb + q is -1
-      const int8_t* srow = g.S8 + (size_t)m * g.lds8 + nb;
-      if (full && (reinterpret_cast<uintptr_t>(srow) & 15) == 0) {
-        const uint4 w = __ldg(reinterpret_cast<const uint4*>(srow));
-        const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint32_t sg = (wv[k] >> 7) & 0x01010101u;  // sign bit of each byte
-          neg |= ((sg * 0x01020408u) >> 24 & 0xFu) << (4 * k);
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 16; ++q)
-          if (mvalid && nb + q < g.N && srow[q] < 0) neg |= 1u << q;
-      }
       float d[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const bool in = mvalid && nb + q < g.N;
-        const float z = v[q] + (nb + q < g.N ? __ldg(g.bias + nb + q) : 0.0f);
-        const float sgn = (neg >> q) & 1u ? -1.0f : 1.0f;
+        const float z = v[q] + bias_s[lb + q];
+        const float sgn = (neg[c] >> q) & 1u ? -1.0f : 1.0f;
         float ls, sm;
         logsig_pair(sgn * z, ls, sm);
         if (in) rowsum += ls;
@@ -264,56 +398,42 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
       }
     } else if constexpr (op == kOpGA) {
       // the adjoint of the pre-activation: (D V)[m][k] * act'(a), act' from H
-      float hv[16];
-      const bf16* hrow = g.aux + (size_t)m * g.ldaux + nb;
-      if (full) {
-        const uint4 q0 = __ldg(reinterpret_cast<const uint4*>(hrow)), q1 = __ldg(reinterpret_cast<const uint4*>(hrow) + 1);
-        const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-#pragma unroll
-        for (int q = 0; q < 8; ++q) hv[2 * q] = __uint_as_float(w[q] << 16), hv[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) hv[q] = (mvalid && nb + q < g.N) ? __bfloat162float(hrow[q]) : 0.0f;
-      }
+      const uint32_t w[8] = {hpre[2 * c].x, hpre[2 * c].y, hpre[2 * c].z, hpre[2 * c].w,
+                             hpre[2 * c + 1].x, hpre[2 * c + 1].y, hpre[2 * c + 1].z, hpre[2 * c + 1].w};
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
+        const float hv = (q & 1) ? __uint_as_float(w[q >> 1] & 0xffff0000u) : __uint_as_float(w[q >> 1] << 16);
         const bool in = mvalid && nb + q < g.N;
-        const float da = g.act == VQMC_ACT_RELU ? (hv[q] > 0.0f ? 1.0f : 0.0f) : hv[q] * (1.0f - hv[q]);
+        const float da = g.act == VQMC_ACT_RELU ? (hv > 0.0f ? 1.0f : 0.0f) : hv * (1.0f - hv);
         const float x = in ? v[q] * da : 0.0f;
         if (in) g.out_t[(size_t)(nb + q) * g.ldt + m] = __float2bfloat16_rn(x);
         cs[q] = x;
       }
-    } else if constexpr (op == kOpDV || op == kOpDW) {
-      float o[16];
+    } else if constexpr (kWgrad) {
+      // staged for the warp's row-wise pass (the ring is free: every MMA has completed)
+      float* G = reinterpret_cast<float*>(smem) + warp * 32 * kStageLd;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) o[q] = gemm_out_kept(op, m, nb + q, g.n, g.h) ? v[q] : 0.0f;
-      float* grow = g.gout + (size_t)m * g.ldg + nb;
-      if (full && (reinterpret_cast<uintptr_t>(grow) & 15) == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          reinterpret_cast<float4*>(grow)[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-      } else if (mvalid) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q)
-          if (nb + q < g.N) grow[q] = o[q];
-      }
+      for (int q = 0; q < 16; ++q) G[lane * kStageLd + 16 * c + q] = v[q];
     } else if constexpr (op == kOpEloc) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        if (mvalid && nb + q < g.N) {
-          const float sgn = g.S8[(size_t)m * g.lds8 + nb + q] > 0 ? 0.5f : -0.5f;
-          rowsum = fmaf(sgn, v[q], rowsum);
-        }
-      }
+      for (int q = 0; q < 16; ++q)
+        if (mvalid && nb + q < g.N) rowsum = fmaf((neg[c] >> q) & 1u ? -0.5f : 0.5f, v[q], rowsum);
     }
     if (want_col) {
       const float w = colsum16(cs, lane);
-      if ((lane & 1) == 0) colbuf[warp * BN + c0 + colsum16_col(lane)] = w;
+      if ((lane & 1) == 0) colbuf[quad * BN + lb + colsum16_col(lane)] = w;
     }
   }
-  if (g.row_part && (op == kOpOut || op == kOpEloc) && mvalid) g.row_part[(size_t)blockIdx.x * g.ldr + m] = rowsum;
+  if constexpr (kWgrad) {
+    __syncwarp();
+    wgrad_block(g, fused, reinterpret_cast<float*>(smem) + warp * 32 * kStageLd, m0 + quad * 32, c0, lane, kl, kh);
+  }
+  constexpr bool kRows = op == kOpOut || op == kOpEloc;
+  if (kRows && half == 1) rowbuf[quad * 32 + lane] = rowsum;
   fence_before();
   __syncthreads();
+  if (kRows && half == 0 && g.row_part && mvalid)
+    g.row_part[(size_t)blockIdx.x * g.ldr + m] = rowsum + rowbuf[quad * 32 + lane];
   if (want_col && tid < BN && n0 + tid < g.N) {
     const float v = colbuf[tid] + colbuf[BN + tid] + colbuf[2 * BN + tid] + colbuf[3 * BN + tid];
     g.col_part[(size_t)blockIdx.y * g.ldc + n0 + tid] = v;
@@ -388,12 +508,12 @@ cudaError_t launch_gemm_tc_bf16(const GemmArgs<bf16>& a, cudaStream_t st) {
   dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM);
   const int two = a.Bm2 ? 1 : 0;
   switch (a.op) {
-    case kOpHidden: gemm_tc_kernel<kOpHidden><<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
-    case kOpOut: gemm_tc_kernel<kOpOut><<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
-    case kOpDV: gemm_tc_kernel<kOpDV><<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
-    case kOpGA: gemm_tc_kernel<kOpGA><<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
-    case kOpDW: gemm_tc_kernel<kOpDW><<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
-    case kOpEloc: gemm_tc_kernel<kOpEloc><<<grid, 128, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
+    case kOpHidden: gemm_tc_kernel<kOpHidden><<<grid, kThreads, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
+    case kOpOut: gemm_tc_kernel<kOpOut><<<grid, kThreads, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
+    case kOpDV: gemm_tc_kernel<kOpDV><<<grid, kThreads, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
+    case kOpGA: gemm_tc_kernel<kOpGA><<<grid, kThreads, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
+    case kOpDW: gemm_tc_kernel<kOpDW><<<grid, kThreads, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
+    case kOpEloc: gemm_tc_kernel<kOpEloc><<<grid, kThreads, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -131,10 +131,24 @@ namespace vqmc {
 vqmc_status set_last_error(vqmc_status s, const std::string& msg) { return fail(s, msg); }
 
 cudaError_t launch_gemm(const vqmc_ctx* c, GemmOp op, int B, const int8_t* d_s, const float* coef, float* grad,
-                        cudaStream_t st) {
+                        cudaStream_t st, const AdamStep* fuse) {
   if (c->prec == VQMC_PREC_BF16) {
     GemmArgs<bf16> a = make_args<bf16>(c, op, B, d_s, coef, grad);
     if (op == kOpEloc) a.Bm = (const bf16*)c->J_hi, a.Bm2 = (const bf16*)c->J_lo;
+    if (fuse && (op == kOpDV || op == kOpDW)) {
+      // the Adam step in the epilogue: W2 (row copy v_s, transposed vt_s) or
+      // W1^T (transposed w_s; the row copy wt_s, shifted by one row, only
+      // for the CUDA-core sampler)
+      const size_t off = op == kOpDV ? (size_t)c->n * c->h + c->h : 0;
+      a.theta = c->theta + off, a.adam_m = c->adam_m + off, a.adam_v = c->adam_v + off;
+      a.gout = nullptr;
+      a.cp_t = (bf16*)(op == kOpDV ? c->vt_s : c->w_s), a.ld_cp_t = c->np;
+      const bool row = op == kOpDV || c->sampler != VQMC_SAMPLER_TENSOR_CORE;
+      a.cp_row = row ? (bf16*)(op == kOpDV ? c->v_s : c->wt_s) : nullptr;
+      a.ld_cp_row = c->hp, a.cp_shift = op == kOpDV ? 0 : 1;
+      a.lr = c->cfg.lr, a.beta1 = c->cfg.beta1, a.beta2 = c->cfg.beta2, a.eps = c->cfg.eps;
+      a.ibc1 = fuse->ibc1, a.ibc2 = fuse->ibc2;
+    }
     // BF16 GEMMs run on the tcgen05 tensor cores only (sm_103a); no fallback
     return launch_gemm_tc_bf16(a, st);
   }
@@ -150,17 +164,20 @@ namespace {
 // Backward of log pi w.r.t. theta with per-sample weights gout (Sec. 2.1,
 // chain rule through the MADE layer of Sec. 2.3).  Requires Sx/St to hold the
 // spins.  Recomputes H instead of keeping it from any earlier forward pass.
+// With fuse set (BF16), the two weight-gradient GEMMs apply that Adam step
+// to W2 and W1^T in their epilogues instead of writing dW2 and dW1^T; both
+// run after every GEMM that reads the old weights (hidden adjoint: W2).
 vqmc_status backward_from_operands(vqmc_ctx* c, int B, const int8_t* d_s, const float* gout, float* grad,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, const AdamStep* fuse = nullptr) {
   const int n = c->n, h = c->h;
   const int mtiles = (B + 127) / 128;
   VQ_CUDA(launch_gemm(c, kOpHidden, B, d_s, nullptr, nullptr, st));
   VQ_CUDA(launch_gemm(c, kOpOut, B, d_s, gout, nullptr, st));
   VQ_CUDA(launch_col_sum(c, n, mtiles, grad + (size_t)2 * n * h + h, st));  // db2
-  VQ_CUDA(launch_gemm(c, kOpDV, B, d_s, nullptr, grad, st));                // dW2
   VQ_CUDA(launch_gemm(c, kOpGA, B, d_s, nullptr, nullptr, st));
   VQ_CUDA(launch_col_sum(c, h, mtiles, grad + (size_t)n * h, st));          // db1
-  VQ_CUDA(launch_gemm(c, kOpDW, B, d_s, nullptr, grad, st));                // dW1^T
+  VQ_CUDA(launch_gemm(c, kOpDV, B, d_s, nullptr, grad, st, fuse));          // dW2
+  VQ_CUDA(launch_gemm(c, kOpDW, B, d_s, nullptr, grad, st, fuse));          // dW1^T
   return VQMC_OK;
 }
 
@@ -516,11 +533,16 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
   // (d) FP64 statistics and score-function coefficients
   VQ_CUDA(launch_stats(c, B, c->E, c->stats, c->coef, st));
   mark(3);
-  // (b) + adjoint: gradient with recomputed hidden activations
-  s = backward_from_operands(c, B, c->S, c->coef, c->grad, st);
+  // (b) + adjoint: gradient with recomputed hidden activations; for BF16 the
+  // weight-gradient GEMMs apply the Adam step to the weights themselves
+  const bool fuse = c->prec == VQMC_PREC_BF16;
+  AdamStep astep{};
+  if (fuse) astep = adam_advance(c);
+  s = backward_from_operands(c, B, c->S, c->coef, c->grad, st, fuse ? &astep : nullptr);
   if (s != VQMC_OK) return s;
   mark(4);
-  VQ_CUDA(launch_adam(c, c->grad, st));
+  if (fuse) VQ_CUDA(launch_adam_bias(c, c->grad, astep, st));
+  else VQ_CUDA(launch_adam(c, c->grad, st));
   // the next step's sampler streams v_s and w_s: have them in L2 (the
   // optimiser's traffic evicted them)
   if (c->sampler == VQMC_SAMPLER_TENSOR_CORE) VQ_CUDA(launch_prefetch_sampler_weights(c, st));
@@ -531,11 +553,11 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
   if (timed) {
     c->timed_steps += 1;
     // sampler (+ operand layouts unless the tensor-core sampler writes them), energy (dense: GEMM +
-    // finish; sparse: [pack,] slices [, slice sum]), stats, 7 gradient kernels, Adam with the
-    // weight-copy refresh + bias Adam, [2 L2 prefetches,] step stats
+    // finish; sparse: [pack,] slices [, slice sum]), stats, 7 gradient kernels, [Adam with the
+    // weight-copy refresh unless fused into the gradient GEMMs,] bias Adam, [2 L2 prefetches,] step stats
     const int sampler = tc ? 1 : 2;
     const int energy = !sparse ? 2 : (tc ? 0 : 1) + 1 + (c->eloc_slices > 1 ? 1 : 0);
-    c->launches += sampler + energy + 1 + 7 + 2 + (tc ? 2 : 0) + 1;
+    c->launches += sampler + energy + 1 + 7 + (fuse ? 1 : 2) + (tc ? 2 : 0) + 1;
   }
   c->iter += 1;
   return VQMC_OK;

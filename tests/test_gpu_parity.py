@@ -308,17 +308,25 @@ def test_logprob_backward_arbitrary_weights_and_autograd():
 
 # -------------------------------------------------------------------- adam
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("h", [30, 32])  # scalar path, and the 16-byte path (h % 4 == 0)
-def test_adam_matches_oracle(h):
+def test_adam_matches_oracle(h, prec):
+    """Three Adam steps (Sec. 5.1) equal the oracle's.  The device gets a
+    gradient that is non-zero outside the MADE masks too: only entries inside
+    the masks are updated (the oracle gets the masked gradient), so the
+    masked weights stay exactly zero."""
     n = 40
     inst = er_instance(n, 0.2, 91)
     theta = inputs.lively_params(n, h, 92)
-    m = make_model(n, h, 4, inst, theta=theta)
+    m = make_model(n, h, 4, inst, precision=prec, theta=theta)
     t0 = masked(theta, n, h).astype(np.float64)
     mo, vo = np.zeros_like(t0), np.zeros_like(t0)
     rng = np.random.default_rng(93)
+    keep = masked(np.ones_like(theta), n, h)
     for t in range(1, 4):
-        g = rng.standard_normal(t0.size).astype(np.float32) * masked(np.ones_like(theta), n, h)
+        g = rng.standard_normal(t0.size).astype(np.float32)
         m.adam(torch.from_numpy(g).cuda())
-        oracle.adam(t0, mo, vo, g.astype(np.float64), t)
-    assert np.allclose(m.get_params().numpy(), t0, rtol=0, atol=2e-6)
+        oracle.adam(t0, mo, vo, (g * keep).astype(np.float64), t)
+    got = m.get_params().numpy()
+    assert np.allclose(got, t0, rtol=0, atol=2e-6)
+    assert np.all(got[keep == 0] == 0)

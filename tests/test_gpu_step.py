@@ -60,6 +60,56 @@ def test_step_matches_oracle_iteration(act):
     assert np.all(np.abs(got - masked(theta, n, h)) <= 1e-3 + 1e-6)
 
 
+@pytest.mark.parametrize("act", ["relu", "sigmoid"])
+def test_bf16_step_fused_adam_matches_grad_then_adam_and_oracle(act):
+    """For BF16 the weight-gradient GEMMs apply the Adam step (Sec. 5.1) in
+    their epilogue.  One vqmc_step equals vqmc_grad (which writes the
+    gradient) followed by vqmc_adam on the same samples, including the
+    refreshed BF16 weight copies (the next samples and log-probs agree), and
+    the new theta equals the oracle's Adam step of the oracle's gradient where
+    the gradient is well above its BF16 noise.  Sizes span several 128 x 128
+    tiles with ragged edges and fully masked weight-gradient tiles."""
+    n, h, B, seed = 300, 200, 256, 5161
+    inst = er_instance(n, 0.05, 111)
+    theta = inputs.lively_params(n, h, 112)
+    a = make_model(n, h, B, inst, act=act, precision="bf16", theta=theta, seed=seed, lr=1e-3)
+    b = make_model(n, h, B, inst, act=act, precision="bf16", theta=theta, seed=seed, lr=1e-3)
+    out = StepStats()
+    a.step(B, out)
+    torch.cuda.synchronize()
+    S, E = a.last_batch(B)
+    S, E = S.clone(), E.clone()
+    g, _ = b.grad(S, E)
+    b.adam(g)
+    torch.cuda.synchronize()
+    ta, tb = a.get_params().numpy(), b.get_params().numpy()
+    assert np.allclose(ta, tb, rtol=1e-6, atol=1e-9)
+    # the weight copies: the next batch and its log-probs agree
+    Sa, lpa = a.sample(B, None, iteration=7)
+    Sb, lpb = b.sample(B, None, iteration=7)
+    assert torch.equal(Sa, Sb)
+    assert np.allclose(a.logprob(Sa).cpu().numpy(), b.logprob(Sb).cpu().numpy(), rtol=1e-5, atol=1e-4)
+    # the oracle: its own samples (equal to the step's), its gradient, one Adam step
+    code = act_code(act, "bf16")
+    P = oracle_params(theta, n, h, "bf16")
+    U = oracle.uniforms(B, n, seed, 0)
+    So, _ = oracle.sample(P, U, code)
+    assert rows_without_near_ties(P, So, U, code, 1e-5).all(), "choose a seed without near-ties"
+    assert np.array_equal(S.cpu().numpy(), So)
+    (dW1, db1, dW2, db2), sto, _ = oracle.vqmc_grad(P, inst, So, code)
+    assert np.allclose([out.mean, out.var, out.min, out.max], sto, rtol=1e-12)
+    go = oracle.made_to_theta(dW1, db1, dW2, db2)
+    t = masked(theta, n, h).astype(np.float64)
+    oracle.adam(t, np.zeros_like(t), np.zeros_like(t), go, 1, lr=1e-3)
+    big = np.abs(go) > 5e-2 * np.abs(go).max()
+    assert big.sum() > 100
+    assert np.allclose(ta.astype(np.float64)[big], t[big], rtol=0, atol=2e-6)
+    assert np.all(np.abs(ta - masked(theta, n, h)) <= 1e-3 + 1e-6)
+    # masked entries stay exactly zero
+    mz = masked(np.ones_like(theta), n, h) == 0
+    assert np.all(ta[mz] == 0)
+
+
 def test_steps_are_deterministic_and_checkpoint_resumes_bit_exact():
     n, h, B = 200, 128, 128
     inst = er_instance(n, 0.03, 111)
