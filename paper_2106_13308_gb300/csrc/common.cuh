@@ -30,7 +30,8 @@ __host__ __device__ inline int degree(int k, int n, int h) {
 __host__ __device__ inline int count_deg_le(int x, int n, int h) {
   if (x < 1) return 0;
   if (n <= 1) return h;
-  long long c = ((long long)x * h + (n - 2)) / (n - 1);
+  const long long p = (long long)x * h + (n - 2);
+  const long long c = p < (1ll << 32) ? (long long)((unsigned)p / (unsigned)(n - 1)) : p / (n - 1);
   return c > h ? h : (int)c;
 }
 

@@ -25,12 +25,14 @@
 // in shared memory until it completes) adds nothing to any logit.
 //
 // CTA = 16 samples, 6 warps: warps 0-3 own TMEM lanes 32w..32w+31 (read Z
-// and the recent pre-activations, prepare the block's logits and recent
-// weights, write the spins); warps 2-3 are the solver (4 lanes per sample,
-// 8 recent units per lane); warp 4 lane 0 streams 128 x 64 BF16 weight tiles
-// with TMA into a 6-stage ring; warp 5 lane 0 issues the MMAs.  Every wait is
-// bounded; after a failed wait the CTA raises the timeout bit and runs on
-// without waiting, so it still finishes.
+// and the recent pre-activations); warps 2-3 are the solver (4 lanes per
+// sample, 8 recent units per lane) and then write the block's spins as the
+// update GEMM's operand; while they solve, warps 0-1 merge the previous
+// block's recent g1 into the Z operand, prepare the next block's logits and
+// recent-unit weights and write out the previous block's spins; warp 4 lane 0
+// streams 128 x 64 BF16 weight tiles with TMA into a 6-stage ring; warp 5
+// lane 0 issues the MMAs.  Every wait is bounded; after a failed wait the CTA
+// raises the timeout bit and runs on without waiting, so it still finishes.
 #include <algorithm>
 
 #include "gemm.cuh"
@@ -236,7 +238,9 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
     u2 = u1, u1 = u0, u0 = u0n, u0n = u0nn;
   }
   // every recent unit is complete: its g1 goes to the staging operand Hr
-  // (2 chunks of 64 units from chunk klo / 64)
+  // (2 chunks of 64 units from chunk klo / 64), once warps 0-1 have moved
+  // the previous block's recent g1 out of it
+  asm volatile("bar.sync 2, 128;" ::: "memory");
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int r = 8 * sub + j;
@@ -316,8 +320,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(smem_u32(&empty[s]), 1);
     }
     mbar_init(smem_u32(zfull), 1);
-    mbar_init(smem_u32(ready), 128);
-    mbar_init(smem_u32(merged), 128);
+    mbar_init(smem_u32(ready), 64);
+    mbar_init(smem_u32(merged), 64);
     mbar_init(smem_u32(drain), 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -499,69 +503,83 @@ __global__ void __launch_bounds__(kThreads, 1)
           g.sbits[((size_t)(b0 >> 5) * n + b * D + e) * 2 + ((b0 >> 4) & 1)] = (uint16_t)w;
         }
     };
+    // The recent units' weights of block bb (W2 rows of its steps, W1 of its
+    // recent units), loaded by warps 0-1 (thread t < 64) into registers
+    // during the previous block's solver and stored into Vr / Wr once the
+    // solver is done.  Vr: thread t owns steps t and t + 64, 5 aligned
+    // 16-byte pieces of W2 from unit klo & ~7; Wr: pieces (unit q % 32,
+    // inputs 8 (q / 32) ..) for q = t + 64 j, so that a warp's transposing
+    // stores hit 32 different units.
+    uint4 gv[2][5], gw[8];
+    auto gather_load = [&](int bb, int t) {
+      const int klo = count_deg_le(bb * D, n, h), R = count_deg_le(bb * D + D, n, h) - klo;
+      const int steps = min(D, n - bb * D), k8 = klo & ~7;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int e = t + 64 * i;
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+          gv[i][c] = (e < steps && k8 + 8 * c < g.hp)
+                         ? __ldg(reinterpret_cast<const uint4*>(g.v + (size_t)(bb * D + e) * g.hp + k8) + c)
+                         : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int q = t + 64 * j, r = q & 31, c = q >> 5;
+        gw[j] = (8 * c < steps && r < R)  // pieces past the last step stay in [0, np)
+                    ? __ldg(reinterpret_cast<const uint4*>(g.w + (size_t)(klo + r) * g.np + (size_t)bb * D) + c)
+                    : make_uint4(0, 0, 0, 0);
+      }
+    };
+    auto gather_store = [&](int bb, int t) {
+      const int klo = count_deg_le(bb * D, n, h);
+      const int steps = min(D, n - bb * D), off = klo & 7;
+      // Vr[e][r] = W2 of step e, unit klo + r (r < 32; zero for units past the
+      // block's recent ones: they complete after the block, masked in W2)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int e = t + 64 * i;
+        if (e >= D) continue;
+        uint32_t w[20];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) w[4 * c] = gv[i][c].x, w[4 * c + 1] = gv[i][c].y, w[4 * c + 2] = gv[i][c].z,
+                                    w[4 * c + 3] = gv[i][c].w;
+        uint32_t d[16];
+#pragma unroll
+        for (int sh = 0; sh < 4; ++sh)
+          if ((off >> 1) == sh) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) d[j] = (off & 1) ? __byte_perm(w[sh + j], w[sh + j + 1], 0x5432) : w[sh + j];
+          }
+        uint4* dst = reinterpret_cast<uint4*>(Vr + e * kLdW);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dst[j] = make_uint4(d[4 * j], d[4 * j + 1], d[4 * j + 2], d[4 * j + 3]);
+      }
+      // Wr[e][r] = W1 of unit klo + r, input of step e (zero for r >= R)
+      unsigned short* sw = reinterpret_cast<unsigned short*>(Wr);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int q = t + 64 * j, r = q & 31, c = q >> 5;
+        if (8 * c >= D) continue;
+        const uint32_t w[4] = {gw[j].x, gw[j].y, gw[j].z, gw[j].w};
+#pragma unroll
+        for (int tt = 0; tt < 8; ++tt) {
+          const int e = 8 * c + tt;
+          sw[e * kLdW + r] = e < steps ? (unsigned short)(w[tt >> 1] >> (16 * (tt & 1))) : (unsigned short)0;
+        }
+      }
+    };
     logits(0, tid, 128);
+    if (warp < 2) {
+      gather_load(0, tid);
+      gather_store(0, tid);
+    }
     for (int b = 0; b < nblk; ++b) {
       const Blk B = blk_of(b, n, h, D, ntiles, nblk);
       const int klo = B.klo, khi = B.khi;
       const int R = khi - klo;  // <= kRmax (checked by the host)
       const int steps = min(D, n - b * D);
-      // (a) the recent units' weights and completion steps (while the MMAs
-      // of this block's critical part run)
-      // 16-byte global loads, all issued before the shared-memory stores (the
-      // gather sits on the critical path between two solver phases)
-      {
-        unsigned short* sv = reinterpret_cast<unsigned short*>(Vr);
-        unsigned short* sw = reinterpret_cast<unsigned short*>(Wr);
-        // W2 rows i0..i0+D-1, units [klo, klo+32): 5 aligned 16-byte pieces per row from unit k8
-        const int k8 = klo & ~7;
-        constexpr int kPV = 5;
-        const int nv = D * kPV;                      // pieces of W2
-        const int nw = kRmax * (D / 8);              // pieces of W1: 32 units x D inputs
-        uint4 pv[5], pw[4];
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-          const int q = tid + 128 * j;
-          const int e = q / kPV, c = q % kPV;
-          pv[j] = (q < nv && e < steps && k8 + 8 * c < g.hp)
-                      ? __ldg(reinterpret_cast<const uint4*>(g.v + (size_t)(b * D + e) * g.hp + k8) + c)
-                      : make_uint4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int q = tid + 128 * j;
-          const int r = q / (D / 8), c = q % (D / 8);
-          pw[j] = (q < nw && r < R && 8 * c < steps)  // pieces past the last step stay in [0, np)
-                      ? __ldg(reinterpret_cast<const uint4*>(g.w + (size_t)(klo + r) * g.np + (size_t)b * D) + c)
-                      : make_uint4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-          const int q = tid + 128 * j;
-          if (q < nv) {
-            const int e = q / kPV, c = q % kPV;
-            const uint32_t w[4] = {pv[j].x, pv[j].y, pv[j].z, pv[j].w};
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-              const int r = k8 + 8 * c + t - klo;  // recent unit index of this element
-              if (r >= 0 && r < kRmax)
-                sv[e * kLdW + r] = (r < R && e < steps) ? (unsigned short)(w[t >> 1] >> (16 * (t & 1))) : (unsigned short)0;
-            }
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int q = tid + 128 * j;
-          if (q < nw) {
-            const int r = q / (D / 8), c = q % (D / 8);
-            const uint32_t w[4] = {pw[j].x, pw[j].y, pw[j].z, pw[j].w};
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-              const int e = 8 * c + t;
-              sw[e * kLdW + r] = e < steps ? (unsigned short)(w[t >> 1] >> (16 * (t & 1))) : (unsigned short)0;
-            }
-          }
-        }
-      }
+      // (a) the recent units' completion steps (their weights are in Vr / Wr)
       for (int q = tid; q < (kRmax - R) * kS; q += 128) Pr[R * kS + q] = 0.0f;
       for (int e = tid; e < D + 5; e += 128) {  // CU[e] = unit completing at step e - 2
         const int x = b * D + e - 2;             // its degree would be x + 1
@@ -572,8 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         CU[e] = u;
       }
-      // (b) Z and the recent pre-activations from tensor memory; block b-1's
-      // recent g1 from the staging operand into the GEMM operand
+      // (b) Z and the recent pre-activations from tensor memory
       wait_or_abort(smem_u32(zfull), (uint32_t)(b & 1), abort, g.err);
       __syncwarp();
       fence_after();
@@ -605,21 +622,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-      if (b > 0) {
-        const int kprev = count_deg_le((b - 1) * D, n, h), cb = kprev >> 6;
-        for (int q = tid; q < (klo - kprev) * kS; q += 128) {
-          const int k = kprev + q / kS, s = q % kS;
-          const uint32_t o = sw128_offset(s, k & 63);
-          bf16* src = reinterpret_cast<bf16*>(Hr + ((k >> 6) - cb) * 2048 + o);
-          *reinterpret_cast<bf16*>(Hs + (k >> 6) * 2048 + o) = *src;
-          *src = __float2bfloat16_rn(0.0f);  // Hr is zero outside the current recent units
-        }
-      }
-      fence_proxy_async();
-      fence_before();
-      mbar_arrive(smem_u32(merged));
+      fence_before();  // the tensor-memory reads precede the next MMAs into Z (after merged)
       asm volatile("bar.sync 1, 128;" ::: "memory");
-      // (c) the D draws of the block (warps 2-3); warps 0-1 meanwhile
+      // (c) the D draws of the block (warps 2-3), then the block's spins as
+      // the update GEMM's operand; warps 0-1 meanwhile
       if (warp >= 2) {
         const bool relu = g.act == VQMC_ACT_RELU;
         const float* L = LG + (b & 1) * kDrows * kS;
@@ -631,25 +637,45 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (relu) solve<VQMC_ACT_RELU, false>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, HfS, Hr, s_me, sub, klo, R, steps, lp);
           else solve<VQMC_ACT_SIGMOID, false>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, HfS, Hr, s_me, sub, klo, R, steps, lp);
         }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        // (d) 8 spins of one sample per 16-byte store (+1 = 0x3F80, -1 = 0xBF80)
+        unsigned char* ss = Ss + (b & 1) * (kDmax / 64) * 2048;
+        for (int q = tid - 64; q < kS * (D / 8); q += 64) {
+          const int s = q / (D / 8), e = 8 * (q % (D / 8));
+          const uint32_t bits = ~(sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31));  // bit set: spin -1
+          uint32_t w[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+            w[p] = 0x3F803F80u | ((bits >> (2 * p)) & 1u) << 15 | ((bits >> (2 * p + 1)) & 1u) << 31;
+          *reinterpret_cast<uint4*>(ss + (e >> 6) * 2048 + sw128_offset(s, e & 63)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        fence_proxy_async();
+        fence_before();
+        mbar_arrive(smem_u32(ready));
       } else {
+        // block b-1's recent g1 from the staging operand into the GEMM
+        // operand (the block's Z GEMM has read Hr: zfull), then release Hr
+        // to the solver and the operand to the next Z GEMM
+        if (b > 0) {
+          const int kprev = count_deg_le((b - 1) * D, n, h), cb = kprev >> 6;
+          for (int q = tid; q < (klo - kprev) * kS; q += 64) {
+            const int k = kprev + q / kS, s = q % kS;
+            const uint32_t o = sw128_offset(s, k & 63);
+            bf16* src = reinterpret_cast<bf16*>(Hr + ((k >> 6) - cb) * 2048 + o);
+            *reinterpret_cast<bf16*>(Hs + (k >> 6) * 2048 + o) = *src;
+            *src = __float2bfloat16_rn(0.0f);  // Hr is zero outside the current recent units
+          }
+        }
+        fence_proxy_async();
+        fence_before();
+        mbar_arrive(smem_u32(merged));
+        asm volatile("bar.arrive 2, 128;" ::: "memory");
         if (b + 1 < nblk) logits(b + 1, tid, 64);
         if (b > 0) write_spins(b - 1, tid, 64);
+        if (b + 1 < nblk) gather_load(b + 1, tid);
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (b + 1 < nblk) gather_store(b + 1, tid);
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      // (d) the block's spins as the update GEMM's operand
-      {
-        const uint32_t* sb = SB + (b & 1) * kS * (kDmax / 32);
-        unsigned char* ss = Ss + (b & 1) * (kDmax / 64) * 2048;
-        for (int q = tid; q < kS * D; q += 128) {
-          const int s = q / D, e = q % D;
-          const bool up = (sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u;
-          *reinterpret_cast<bf16*>(ss + (e >> 6) * 2048 + sw128_offset(s, e & 63)) =
-              __float2bfloat16_rn(up ? 1.0f : -1.0f);
-        }
-      }
-      fence_proxy_async();
-      fence_before();
-      mbar_arrive(smem_u32(ready));
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
     write_spins(nblk - 1, tid, 128);
