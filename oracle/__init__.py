@@ -72,6 +72,7 @@ def _load():
             lib.vo_sample_incremental.argtypes = [I, I, I, I, P, P, P, P, P, P, P]
             lib.vo_energy_sparse.argtypes = [I, I, P, P, P, P, P, P]
             lib.vo_energy_dense.argtypes = [I, I, P, P, P, P]
+            lib.vo_energy_tim_offdiag.argtypes = [I, I, I, I, P, P, P, P, P, P, P]
             lib.vo_cut.argtypes = [I, I, P, P, P, P, P]
             lib.vo_maxcut_bruteforce.restype = D
             lib.vo_maxcut_bruteforce.argtypes = [I, P, P, P]
@@ -231,9 +232,34 @@ def energy_dense(J, S, field=None) -> np.ndarray:
 
 
 def energy(inst, S) -> np.ndarray:
+    """Diagonal (Ising) part of the local energy."""
     if inst["kind"] == "dense":
         return energy_dense(inst["J"], S, inst.get("field"))
     return energy_sparse(inst, S)
+
+
+def energy_tim_offdiag(params, S, alpha, act=RELU) -> np.ndarray:
+    """-sum_i alpha_i sqrt(pi(s^(i)) / pi(s)) for each sample (transverse field
+    of Eq. (hamiltonian), psi = sqrt(pi)); n + 1 forward passes per sample."""
+    lib = _load()
+    W1, b1, W2, b2 = _made(params)
+    h, n = W1.shape
+    S = _i8(S).reshape(-1, n)
+    alpha = _f64(alpha).reshape(-1)
+    assert alpha.size == n
+    E = np.zeros(S.shape[0])
+    lib.vo_energy_tim_offdiag(S.shape[0], n, h, act, _p(W1), _p(b1), _p(W2), _p(b2), _p(alpha), _p(S), _p(E))
+    return E
+
+
+def local_energy(params, inst, S, act=RELU) -> np.ndarray:
+    """Local energy of each sample: the diagonal energy, plus the transverse
+    field's off-diagonal part when the instance has "alpha" (the model's
+    parameters are needed only then)."""
+    E = energy(inst, S)
+    if inst.get("alpha") is not None:
+        E = E + energy_tim_offdiag(params, S, inst["alpha"], act)
+    return E
 
 
 def cut(inst, S) -> np.ndarray:
@@ -287,7 +313,7 @@ def logprob_grad(params, S, coef, act=RELU):
 
 def vqmc_grad(params, inst, S, act=RELU):
     """Score-function gradient of one batch: stats of E, then sum_b c_b grad log pi."""
-    E = energy(inst, S)
+    E = local_energy(params, inst, S, act)
     st, coef = stats(E)
     return logprob_grad(params, S, coef, act), st, E
 

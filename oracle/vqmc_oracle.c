@@ -292,6 +292,46 @@ void vo_energy_dense(int B, int n, const double* J, const double* field, const i
   }
 }
 
+/* Off-diagonal part of the local energy of the transverse-field Ising model,
+ * Eq. (hamiltonian): the term -sum_i alpha_i X_i joins x to the n states x^(i)
+ * that differ from x in spin i only (matrix entries, Eq. (e:tim):
+ * H_{x, x^(i)} = -alpha_i).  With the wave function psi = sqrt(pi) of the
+ * autoregressive model (Sec. 2.1), the local energy sum_y H_xy psi(y)/psi(x)
+ * gets from these entries
+ *     E_off(x) = -sum_i alpha_i sqrt(pi(x^(i)) / pi(x))
+ *              = -sum_i alpha_i exp((log pi(x^(i)) - log pi(x)) / 2),
+ * each log pi(x^(i)) one more full forward pass (n + 1 per sample).  The
+ * diagonal part (-beta_i Z_i, -beta_ij Z_i Z_j) is an Ising energy as above,
+ * with J_ij = -beta_ij and h_i = -beta_i. */
+static double logprob_one(int n, int h, int act, const double* W1, const double* b1, const double* W2,
+                          const double* b2, const int8_t* s, double* z) {
+  vo_forward(n, h, act, W1, b1, W2, b2, s, NULL, z);
+  double lp = 0.0;
+  for (int i = 0; i < n; ++i) lp += log_sigmoid((double)s[i] * z[i]);
+  return lp;
+}
+
+void vo_energy_tim_offdiag(int B, int n, int h, int act, const double* W1, const double* b1, const double* W2,
+                           const double* b2, const double* alpha, const int8_t* S, double* E) {
+#pragma omp parallel for schedule(static)
+  for (int b = 0; b < B; ++b) {
+    double* z = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    int8_t* t = (int8_t*)malloc((size_t)(n > 0 ? n : 1));
+    memcpy(t, S + (size_t)b * n, (size_t)n);
+    const double lp0 = logprob_one(n, h, act, W1, b1, W2, b2, t, z);
+    double e = 0.0;
+    for (int i = 0; i < n; ++i) {
+      t[i] = (int8_t)(-t[i]);
+      const double lpi = logprob_one(n, h, act, W1, b1, W2, b2, t, z);
+      t[i] = (int8_t)(-t[i]);
+      e -= alpha[i] * exp(0.5 * (lpi - lp0));
+    }
+    E[b] = e;
+    free(t);
+    free(z);
+  }
+}
+
 /* Cut value of the partition given by s: sum over edges of w_ij [s_i != s_j]
  * (Max-Cut, Sec. 2.4), counted directly from the edge list. */
 void vo_cut(int B, int n, const int* row_ptr, const int* col, const double* w, const int8_t* S,

@@ -5,7 +5,7 @@ draws problem instances, initial parameters and explicit uniforms as plain
 data.  It holds none of the method's arithmetic (no masks, no forward pass, no
 energies): each side applies the MADE masks and evaluates everything itself.
 
-Instances follow the paper's workloads (Sec. 5.1) and the five benchmark
+Instances follow the paper's workloads (Sec. 5.1) and the benchmark
 configurations used throughout the repository:
 
 * ``paper_maxcut``: adjacency from (B + B^T)/2, B_ij ~ Bernoulli(0.5), rounded
@@ -16,6 +16,10 @@ configurations used throughout the repository:
   loops and multi-edges.
 * ``sk``: Sherrington-Kirkpatrick couplings J_ij = J_ji ~ N(0, 1/n), zero
   diagonal, as a dense float32 matrix.
+* ``tim``: the transverse-field Ising model of Eq. (hamiltonian) with the
+  paper's disorder (Sec. 5): beta_i, beta_ij ~ U(-1, 1), alpha_i ~ U(0, 1),
+  drawn once.  Stored as the library's Ising form E = sum_{i<j} J_ij s_i s_j
+  + sum_i h_i s_i with J = -beta, h = -beta_i (dense), plus ``alpha``.
 
 Sparse instances are stored as the strict upper triangle in CSR form
 (``row_ptr`` int32 [n+1], ``col`` int32 [m] with col > row, ``w`` int32 or
@@ -147,6 +151,19 @@ def sk(n: int, seed: int) -> dict:
     return {"kind": "dense", "n": int(n), "J": J.astype(np.float32), "field": None}
 
 
+def tim(n: int, seed: int) -> dict:
+    """Transverse-field Ising instance (Eq. (hamiltonian), disorder of Sec. 5):
+    dense J = -beta (beta_ij = beta_ji ~ U(-1, 1), zero diagonal), field
+    h = -beta_i (beta_i ~ U(-1, 1)), alpha_i ~ U(0, 1), all float32."""
+    rng = _rng(seed)
+    beta2 = np.triu(rng.uniform(-1.0, 1.0, size=(n, n)), 1)
+    beta2 = beta2 + beta2.T
+    beta1 = rng.uniform(-1.0, 1.0, size=n)
+    alpha = rng.uniform(0.0, 1.0, size=n)
+    return {"kind": "dense", "n": int(n), "J": (-beta2).astype(np.float32), "field": (-beta1).astype(np.float32),
+            "alpha": alpha.astype(np.float32)}
+
+
 def dense_from_sparse(inst: dict) -> np.ndarray:
     """The same couplings as a dense symmetric float64 matrix."""
     n = inst["n"]
@@ -195,7 +212,7 @@ def spins(B: int, n: int, seed: int) -> np.ndarray:
 # ------------------------------------------------------ named workloads
 
 def config(name: str) -> dict:
-    """The five benchmark workloads, as plain descriptions (sizes, seeds)."""
+    """The benchmark workloads, as plain descriptions (sizes, seeds)."""
     table = {
         # G(20, 0.5), unit weights, sigmoid hidden units, h = 40, B = 1024
         "maxcut_er20": dict(n=20, h=40, B=1024, act="sigmoid", graph="er", p=0.5, weights="unit",
@@ -209,6 +226,10 @@ def config(name: str) -> dict:
         # SK n = 2000 dense J ~ N(0, 1/n), h = 2000, B = 8192
         "sk2000": dict(n=2000, h=2000, B=8192, act="relu", graph="sk", graph_seed=7,
                        param_seed=8, w_std=0.01),
+        # transverse-field Ising, n = 500 (the paper's largest TIM size, Tables 1 and 2),
+        # h = 5 (ln n)^2 = 193 (Sec. 5), B = 1024
+        "tim500": dict(n=500, h=193, B=1024, act="relu", graph="tim", graph_seed=9,
+                       param_seed=10, w_std=0.01),
     }
     return dict(table[name], name=name)
 
@@ -217,6 +238,8 @@ def make_instance(cfg: dict) -> dict:
     n, g = cfg["n"], cfg["graph"]
     if g == "sk":
         return sk(n, cfg["graph_seed"])
+    if g == "tim":
+        return tim(n, cfg["graph_seed"])
     if g == "er":
         e = erdos_renyi(n, cfg["p"], cfg["graph_seed"])
     elif g == "regular":
