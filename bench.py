@@ -12,6 +12,11 @@ and reported under "fp32".  Under torchrun with N > 1 every rank runs an
 independent replica (the path has no collective on one GPU per rank); the
 value is the sum over ranks of iterations / max rank time.
 
+A second workload, the transverse-field Ising model at the paper's largest TIM
+size (n = 500, h = 5 (ln n)^2 = 193, B = 1024; Tables 1 and 2), is timed the
+same way and reported under "tim": its local energy adds the off-diagonal
+part, n + 1 log-prob evaluations per sample through the tensor-core GEMMs.
+
 --impl reference times the FP64 CPU oracle on the host cores instead (a
 bounded sub-batch per step, scaled linearly to the full batch).
 """
@@ -33,6 +38,9 @@ if ROOT not in sys.path:
 METRIC = "VQMC iterations/s and exact samples/s at N=10,000 (BF16+FP32 vs plain FP32, 1 GB300)"
 UNIT = "it/s"
 WORKLOAD = "maxcut_er10000"
+TIM_WORKLOAD = "tim500"
+# Table 1: MADE + ADAM + AUTO on TIM, n = 500, 300 iterations in 49.62 s on one V100
+PAPER_TIM500_MS_PER_ITER = 49.62 / 300 * 1000.0
 
 
 def _dist_env():
@@ -273,6 +281,7 @@ def main():
     ap.add_argument("--config", default=WORKLOAD)
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-tim", action="store_true", help="skip the transverse-field Ising workload")
     args = ap.parse_args()
     rank, world, local = _dist_env()
     W = max(args.warmup, 3)
@@ -365,6 +374,33 @@ def main():
                 "part_ms": {k: v / max(steps32, 1) for k, v in parts32.items()}}
         del m32
 
+    tim = None
+    if not args.no_tim:
+        torch.cuda.empty_cache()
+        tcfg, tinst = _workload(TIM_WORKLOAD)
+        tB = tcfg["B"]
+        mt = _make(tcfg, tinst, "bf16")
+        kt = max(3, K // 2)
+        mst, partst, stepst, launchest = _timed_steps(mt, tB, kt, W, dist_on)
+        mst, tval = _replica_rate(mst, kt, world, "cuda")
+        tpart = {k: v / max(stepst, 1) for k, v in partst.items()}
+        # the off-diagonal energy's GEMMs: (n + 1) B rows, each a masked forward
+        # pass of h n multiply-adds over both layers
+        tflops = 2.0 * tcfg["h"] * tcfg["n"] * tB * (tcfg["n"] + 1)
+        tach = tflops / (tpart["energy"] / 1000.0) / 1e12
+        tim = {"workload": f"{TIM_WORKLOAD}: transverse-field Ising, n={tcfg['n']}, dense beta_ij, beta_i ~ U(-1,1), "
+                           f"alpha_i ~ U(0,1) (Sec. 5); MADE h={tcfg['h']} {tcfg['act']}; batch {tB}; BF16",
+               "value": tval, "unit": UNIT, "ms_per_step": mst / kt, "samples_per_s": tval * tB, "steps": kt,
+               "part_ms": tpart, "gpu_launches": launchest,
+               "roofline_energy": {"bound": "tensor", "achieved": tach, "peak": peak, "unit": "TFLOP/s",
+                                   "frac": tach / peak, "peak_source": peak_src,
+                                   "algorithmic": f"2*h*n*B*(n+1) = {tflops:.3e} flop per step (the log-prob "
+                                                  "GEMMs of every flipped state), over the energy part's time"},
+               "paper_v100_ms_per_step": PAPER_TIM500_MS_PER_ITER,
+               "paper_note": "Table 1 (one V100, another machine): context, not the target",
+               "device_error_flags": mt.check()}
+        del mt
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = _cpu_baseline(cfg, inst)
@@ -377,7 +413,7 @@ def main():
                 "samples_per_s": value * B,
                 # exact samples per second of the sampler alone (uniforms are drawn inside it)
                 "sampler_samples_per_s": world * B / (sample_ms / 1000.0),
-                "part_ms": part_ms, "fp32": fp32,
+                "part_ms": part_ms, "fp32": fp32, "tim": tim,
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clk, "device_error_flags": flags}

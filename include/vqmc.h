@@ -120,7 +120,13 @@ typedef struct {
  * strict upper triangle, each undirected edge once), w [nnz] int32 or float32
  * per kind.  Dense kind: J float32 [n][n] symmetric with zero diagonal.
  * field: h_i, [n] of the weight type (int32 for SPARSE_I32, float32
- * otherwise), or NULL for h = 0. */
+ * otherwise), or NULL for h = 0.
+ * alpha: the transverse field of the transverse-field Ising model,
+ * Eq. (hamiltonian): H = -sum_i (alpha_i X_i + beta_i Z_i)
+ * - sum_{i<j} beta_ij Z_i Z_j, with the diagonal part given as above
+ * (J_ij = -beta_ij, h_i = -beta_i); float32 [n], every alpha_i >= 0 and
+ * finite (the paper's sign condition, Sec. 2.4), or NULL for none.  Only with
+ * the float32 kinds (SPARSE_F32, DENSE_F32); INVALID_ARG otherwise. */
 typedef struct {
   int32_t kind; /* VQMC_HAM_* */
   int32_t n;
@@ -131,6 +137,7 @@ typedef struct {
   const void* w;
   const void* field;
   const float* J;
+  const float* alpha;
 } vqmc_instance;
 
 /* Result of one vqmc_step, FP64 statistics of the batch's local energies
@@ -190,11 +197,16 @@ vqmc_status vqmc_uniforms(vqmc_ctx* ctx, int32_t B, uint64_t iteration, float* d
 vqmc_status vqmc_sample(vqmc_ctx* ctx, int32_t B, const float* d_u, uint64_t iteration, int8_t* d_s,
                         float* d_logp, vqmc_stream stream);
 
-/* Diagonal local energy l(s) = H_ss (Sec. 2.1, Sec. 2.4) of B configurations
- * d_s int8 [B][n]: E_b = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i.  d_e is
- * int32 [B] (exact) for VQMC_HAM_SPARSE_I32 and float32 [B] otherwise.  The
- * dense kind runs S.J on the tensor cores in BF16 with a hi/lo split of J
- * (error stated in the design notes) in BF16 precision, FP32 otherwise. */
+/* Local energy l(s) = sum_y H_sy psi(y) / psi(s), psi = sqrt(pi) (Sec. 2.1),
+ * of B configurations d_s int8 [B][n].  The diagonal part (Sec. 2.4):
+ * E_b = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i.  d_e is int32 [B] (exact)
+ * for VQMC_HAM_SPARSE_I32 and float32 [B] otherwise.  The dense kind runs
+ * S.J on the tensor cores in BF16 with a hi/lo split of J (error stated in the
+ * design notes) in BF16 precision, FP32 otherwise.  With a transverse field
+ * alpha, also -sum_i alpha_i sqrt(pi(s^(i)) / pi(s)) (s^(i): spin i flipped,
+ * Eq. (e:tim)): the n flipped states of every sample and the sample itself
+ * go through the model's log-prob GEMMs in chunks of rows, so this costs
+ * about n + 1 log-prob evaluations per sample. */
 vqmc_status vqmc_local_energy(vqmc_ctx* ctx, int32_t B, const int8_t* d_s, void* d_e, vqmc_stream stream);
 
 /* log pi(s_b) (Sec. 2.3) of B configurations by the full masked forward

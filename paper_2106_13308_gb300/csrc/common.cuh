@@ -94,6 +94,17 @@ struct vqmc_ctx {
   float* J = nullptr;     // dense [n][np] float
   void* J_hi = nullptr;   // dense split, [n][np] bf16
   void* J_lo = nullptr;
+  // transverse field alpha [n] (or null) and the workspaces of its
+  // off-diagonal local energy: rows are (sample b, flipped spin i) pairs,
+  // g = b (n + 1) + i, i = n standing for the sample itself; tim_rows rows
+  // per chunk
+  float* alpha = nullptr;
+  int tim_rows = 0;
+  void* tim_Sx = nullptr;         // [tim_rows][np] spins of the rows (GEMM operand)
+  int8_t* tim_S8 = nullptr;       // [tim_rows][np] the same as int8
+  void* tim_H = nullptr;          // [tim_rows][hp] hidden activations
+  float* tim_row_part = nullptr;  // [ceil(n/128)][tim_rows] log pi partial sums
+  float* tim_lp = nullptr;        // [Bmax][n + 1] log pi of every row
 
   // workspaces (element type per precision unless noted)
   int8_t* S = nullptr;     // int8 [Bmax][n] samples of vqmc_step
@@ -147,6 +158,12 @@ cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64
 cudaError_t launch_eloc_sparse(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st,
                                bool packed = false);
 cudaError_t launch_eloc_dense_finish(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st);
+// ---- tim.cu: adds the transverse field's off-diagonal local energy to d_e
+// (float [B]); *launches (if not null) receives the number of kernels
+cudaError_t launch_tim_offdiag(const vqmc_ctx* c, int B, const int8_t* d_s, float* d_e, cudaStream_t st,
+                               int* launches = nullptr);
+// rows per chunk of the flipped states for at most Bmax samples
+int tim_chunk_rows(int Bmax, int n);
 cudaError_t launch_stats(const vqmc_ctx* c, int B, const void* d_e, double* d_stats, float* d_coef,
                          cudaStream_t st);
 cudaError_t launch_spins_to_operands(const vqmc_ctx* c, int B, const int8_t* d_s, void* Sx, void* St,

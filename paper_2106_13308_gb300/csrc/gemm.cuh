@@ -31,7 +31,7 @@ struct GemmArgs {
   const float* coef;   // [M] or null
   T* out;              // row-major [M][ldo]
   int ldo;
-  T* out_t;            // transposed [N][ldt]
+  T* out_t;            // transposed [N][ldt] (kOpHidden: optional)
   int ldt;
   const T* aux;        // [M][ldaux] (H for kOpGA)
   int ldaux;

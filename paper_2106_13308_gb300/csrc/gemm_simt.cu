@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const GemmArgs<T> g) {
           v = g.act == VQMC_ACT_RELU ? fmaxf(v, 0.0f) : sigmoidf_(v);
           const T tv = of_f<T>(v);
           g.out[(size_t)m * g.ldo + nn] = tv;
-          g.out_t[(size_t)nn * g.ldt + m] = tv;
+          if (g.out_t) g.out_t[(size_t)nn * g.ldt + m] = tv;
         }
       }
     }

@@ -368,9 +368,10 @@ __global__ void __launch_bounds__(kThreads, 2) gemm_tc_kernel(const __grid_const
         for (int q = 0; q < 16; ++q)
           if (nb + q < g.N) g.out[(size_t)m * g.ldo + nb + q] = __float2bfloat16_rn(x[q]);
       }
+      if (g.out_t)
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (mvalid && nb + q < g.N) g.out_t[(size_t)(nb + q) * g.ldt + m] = __float2bfloat16_rn(x[q]);
+        for (int q = 0; q < 16; ++q)
+          if (mvalid && nb + q < g.N) g.out_t[(size_t)(nb + q) * g.ldt + m] = __float2bfloat16_rn(x[q]);
     } else if constexpr (op == kOpOut) {
       float d[16];
 #pragma unroll

@@ -48,6 +48,10 @@ uint64_t fnv1a(uint64_t h, const void* p, size_t bytes) {
 
 constexpr int64_t kMaxTimedSteps = 4096;
 
+// the layouts the Python binding mirrors
+static_assert(sizeof(vqmc_config) == 48 && sizeof(vqmc_instance) == 64 && sizeof(vqmc_step_stats) == 48,
+              "C ABI structure layout");
+
 size_t esize(const vqmc_ctx* c) { return c->prec == VQMC_PREC_BF16 ? 2 : 4; }
 
 cudaStream_t S(vqmc_stream s) { return (cudaStream_t)s; }
@@ -214,6 +218,13 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
   } else {
     return fail(VQMC_ERR_INVALID_ARG, "bad instance kind");
   }
+  if (inst->alpha) {
+    if (kind == VQMC_HAM_SPARSE_I32)
+      return fail(VQMC_ERR_INVALID_ARG, "a transverse field needs a float32 instance kind");
+    for (int i = 0; i < n; ++i)
+      if (!(inst->alpha[i] >= 0.0f) || !std::isfinite(inst->alpha[i]))
+        return fail(VQMC_ERR_INVALID_ARG, "alpha must be finite and >= 0");
+  }
   if (pad_up(h) > 2048) return fail(VQMC_ERR_UNSUPPORTED, "this build samples with h <= 2048");
   if (cfg->sampler > VQMC_SAMPLER_TENSOR_CORE) return fail(VQMC_ERR_INVALID_ARG, "bad sampler");
 
@@ -340,6 +351,19 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
       return cleanup_fail(VQMC_ERR_CUDA, "copy of the field failed");
     hsh = fnv1a(hsh, inst->field, (size_t)n * 4);
   }
+  if (inst->alpha) {
+    VQ_ALLOC(c->alpha, (size_t)n * 4);
+    if (cudaMemcpy(c->alpha, inst->alpha, (size_t)n * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup_fail(VQMC_ERR_CUDA, "copy of alpha failed");
+    hsh = fnv1a(hsh, inst->alpha, (size_t)n * 4);
+    c->tim_rows = tim_chunk_rows(Bmax, n);
+    const size_t rows = (size_t)c->tim_rows;
+    VQ_ALLOC(c->tim_Sx, rows * c->np * esize(c));
+    VQ_ALLOC(c->tim_S8, rows * c->np);
+    VQ_ALLOC(c->tim_H, rows * c->hp * esize(c));
+    VQ_ALLOC(c->tim_row_part, (size_t)((n + 127) / 128) * rows * 4);
+    VQ_ALLOC(c->tim_lp, (size_t)Bmax * (n + 1) * 4);
+  }
   c->inst_hash = hsh;
   if (launch_refresh_weights(c, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
     return cleanup_fail(VQMC_ERR_CUDA, "initial weight refresh failed");
@@ -357,7 +381,8 @@ void vqmc_destroy(vqmc_ctx* c) {
   void* ptrs[] = {c->theta, c->adam_m, c->adam_v, c->grad, c->wt_s, c->v_s, c->w_s, c->vt_s, c->row_ptr,
                   c->col, c->w, c->field, c->J, c->J_hi, c->J_lo, c->S, c->E, c->Sx, c->St, c->H, c->Ht,
                   c->D, c->Dt, c->GAt, c->logp, c->coef, c->stats, c->row_part, c->col_part, c->err,
-                  c->step_stats, c->Sbits, c->eloc_part, c->eloc_slice, c->erow};
+                  c->step_stats, c->Sbits, c->eloc_part, c->eloc_slice, c->erow, c->alpha, c->tim_Sx,
+                  c->tim_S8, c->tim_H, c->tim_row_part, c->tim_lp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -426,6 +451,7 @@ vqmc_status vqmc_local_energy(vqmc_ctx* c, int32_t B, const int8_t* d_s, void* d
   } else {
     VQ_CUDA(launch_eloc_sparse(c, B, d_s, d_e, S(stream)));
   }
+  VQ_CUDA(launch_tim_offdiag(c, B, d_s, (float*)d_e, S(stream)));
   return VQMC_OK;
 }
 
@@ -529,6 +555,9 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
   } else {
     VQ_CUDA(launch_eloc_sparse(c, B, c->S, c->E, st, /*packed=*/tc));
   }
+  // transverse field: the off-diagonal part (n + 1 log-prob rows per sample)
+  int tim_launches = 0;
+  VQ_CUDA(launch_tim_offdiag(c, B, c->S, (float*)c->E, st, &tim_launches));
   mark(2);
   // (d) FP64 statistics and score-function coefficients
   VQ_CUDA(launch_stats(c, B, c->E, c->stats, c->coef, st));
@@ -557,7 +586,7 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
     // weight-copy refresh unless fused into the gradient GEMMs,] bias Adam, [2 L2 prefetches,] step stats
     const int sampler = tc ? 1 : 2;
     const int energy = !sparse ? 2 : (tc ? 0 : 1) + 1 + (c->eloc_slices > 1 ? 1 : 0);
-    c->launches += sampler + energy + 1 + 7 + (fuse ? 1 : 2) + (tc ? 2 : 0) + 1;
+    c->launches += sampler + energy + tim_launches + 1 + 7 + (fuse ? 1 : 2) + (tc ? 2 : 0) + 1;
   }
   c->iter += 1;
   return VQMC_OK;

@@ -57,7 +57,8 @@ class Config(ctypes.Structure):
 class Instance(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("nnz", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
-                ("w", ctypes.c_void_p), ("field", ctypes.c_void_p), ("J", ctypes.c_void_p)]
+                ("w", ctypes.c_void_p), ("field", ctypes.c_void_p), ("J", ctypes.c_void_p),
+                ("alpha", ctypes.c_void_p)]
 
 
 class StepStats(ctypes.Structure):
@@ -265,14 +266,15 @@ def _describe(n, h, max_batch, instance, act, precision, lr, beta1, beta2, eps, 
         return a.ctypes.data_as(ctypes.c_void_p)
 
     kind = instance["kind"]
+    alpha = arr(instance.get("alpha"), np.float32)
     if kind == "dense":
         inst = Instance(HAM["dense"], int(n), 0, 0, None, None, None, arr(instance.get("field"), np.float32),
-                        arr(instance["J"], np.float32))
+                        arr(instance["J"], np.float32), alpha)
     else:
         wdt = np.int32 if kind == "sparse_i32" else np.float32
         inst = Instance(HAM[kind], int(n), int(len(instance["col"])), 0, arr(instance["row_ptr"], np.int32),
                         arr(instance["col"], np.int32), arr(instance["w"], wdt), arr(instance.get("field"), wdt),
-                        None)
+                        None, alpha)
     return cfg, inst
 
 
@@ -281,7 +283,7 @@ class VQMC:
 
     ``instance`` is a dict as produced by ``paper_2106_13308_gb300.inputs``
     (kind sparse_i32 / sparse_f32 with row_ptr, col, w[, field]; or dense with
-    J)."""
+    J[, field]; float kinds may add the transverse field ``alpha``)."""
 
     def __init__(self, n, h, max_batch, instance, act="relu", precision="bf16", lr=1e-2, beta1=0.9,
                  beta2=0.999, eps=1e-8, seed=0, sampler="auto", _ctx=None):

@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layouts_match_header():
     from paper_2106_13308_gb300 import vqmc
     assert ctypes.sizeof(vqmc.Config) == 48
-    assert ctypes.sizeof(vqmc.Instance) == 56
+    assert ctypes.sizeof(vqmc.Instance) == 64
     assert ctypes.sizeof(vqmc.StepStats) == 48
 
 
@@ -93,6 +93,20 @@ def test_create_rejects_bad_instances(lib):
     # bad kind
     inst, k3 = _inst(vqmc, kind=9)
     assert lib.vqmc_create(ctypes.byref(cfg), ctypes.byref(inst), ctypes.byref(h)) == vqmc.VQMC_ERR_INVALID_ARG
+
+
+def test_create_rejects_bad_transverse_fields(lib):
+    """alpha needs a float32 energy kind and finite alpha_i >= 0 (Sec. 2.4)."""
+    from paper_2106_13308_gb300 import vqmc
+    cfg = _cfg(vqmc)
+    h = ctypes.c_void_p()
+    for kind, a, msg in [(0, np.ones(10), b"float32"), (1, -np.ones(10), b">= 0"),
+                         (1, np.full(10, np.nan), b">= 0")]:
+        inst, keep = _inst(vqmc, kind=kind)
+        al = np.ascontiguousarray(a, dtype=np.float32)
+        inst.alpha = al.ctypes.data_as(ctypes.c_void_p)
+        assert lib.vqmc_create(ctypes.byref(cfg), ctypes.byref(inst), ctypes.byref(h)) == vqmc.VQMC_ERR_INVALID_ARG
+        assert msg in lib.vqmc_last_error() and not h.value
 
 
 def test_null_context_calls_fail_cleanly(lib):
