@@ -100,11 +100,11 @@ struct vqmc_ctx {
   // per chunk
   float* alpha = nullptr;
   int tim_rows = 0;
-  void* tim_Sx = nullptr;         // [tim_rows][np] spins of the rows (GEMM operand)
-  int8_t* tim_S8 = nullptr;       // [tim_rows][np] the same as int8
-  void* tim_H = nullptr;          // [tim_rows][hp] hidden activations
-  float* tim_row_part = nullptr;  // [ceil(n/128)][tim_rows] log pi partial sums
-  float* tim_lp = nullptr;        // [Bmax][n + 1] log pi of every row
+  float* tim_A = nullptr;         // [Bmax][hp] FP32 hidden pre-activations of the samples
+  int8_t* tim_S8 = nullptr;       // [tim_rows][np] spins of the rows
+  void* tim_H = nullptr;          // [tim_rows][hp] hidden activations of the rows
+  float* tim_row_part = nullptr;  // [ceil(n/128)][tim_ld] partial log pi of every row per output tile
+  long long tim_ld = 0;           // Bmax (n + 1), rounded up to 4
 
   // workspaces (element type per precision unless noted)
   int8_t* S = nullptr;     // int8 [Bmax][n] samples of vqmc_step

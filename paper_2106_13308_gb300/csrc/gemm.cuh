@@ -33,6 +33,15 @@ struct GemmArgs {
   int ldo;
   T* out_t;            // transposed [N][ldt] (kOpHidden: optional)
   int ldt;
+  float* pre;          // kOpHidden, optional: FP32 pre-activations a = S W1^T + b1, [M][ldpre]
+  int ldpre;
+  // kOpOut over the single-flip expansion of the transverse field (rows
+  // g = row0 + m = b (n + 1) + i, i = n the unflipped sample): when set,
+  // an output tile whose columns all precede the flipped spin of every row
+  // of the tile is skipped (those terms equal the unflipped row's), and its
+  // row partials are not written
+  int flip_rows;
+  long long row0;
   const T* aux;        // [M][ldaux] (H for kOpGA)
   int ldaux;
   float* gout;         // FP32 gradient block [M][ldg]

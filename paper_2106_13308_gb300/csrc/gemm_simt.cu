@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const GemmArgs<T> g) {
         const int nn = nb + j;
         if (m < g.M && nn < g.N) {
           float v = acc[i][j] + g.bias[nn];
+          if (g.pre) g.pre[(size_t)m * g.ldpre + nn] = v;
           v = g.act == VQMC_ACT_RELU ? fmaxf(v, 0.0f) : sigmoidf_(v);
           const T tv = of_f<T>(v);
           g.out[(size_t)m * g.ldo + nn] = tv;

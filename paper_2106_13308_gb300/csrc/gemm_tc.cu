@@ -233,6 +233,14 @@ __global__ void __launch_bounds__(kThreads, 2) gemm_tc_kernel(const __grid_const
       }
     return;
   }
+  if (op == kOpOut && g.flip_rows) {
+    // flipped spin of the tile's first row; any unflipped row (i = n) or a
+    // new sample inside the tile needs every column
+    const long long ga = g.row0 + m0;
+    const int ia = (int)(ga % (g.n + 1));
+    const int last = m1 - 1 - m0;  // rows of the tile after the first
+    if (ia + last < g.n && n0 + BN <= ia) return;
+  }
   int klo, khi;
   gemm_k_range(op, n0, n1, g.K, g.n, g.h, &klo, &khi);
   const int kt0 = klo / BK;
@@ -359,6 +367,7 @@ __global__ void __launch_bounds__(kThreads, 2) gemm_tc_kernel(const __grid_const
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const float a = v[q] + bias_s[lb + q];
+        if (g.pre && mvalid && nb + q < g.N) g.pre[(size_t)m * g.ldpre + nb + q] = a;
         x[q] = g.act == VQMC_ACT_RELU ? fmaxf(a, 0.0f) : sigmoidf_(a);
       }
       if (full) {
@@ -374,16 +383,24 @@ __global__ void __launch_bounds__(kThreads, 2) gemm_tc_kernel(const __grid_const
           if (mvalid && nb + q < g.N) g.out_t[(size_t)(nb + q) * g.ldt + m] = __float2bfloat16_rn(x[q]);
     } else if constexpr (op == kOpOut) {
       float d[16];
+      if (g.coef) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const bool in = mvalid && nb + q < g.N;
-        const float z = v[q] + bias_s[lb + q];
-        const float sgn = (neg[c] >> q) & 1u ? -1.0f : 1.0f;
-        float ls, sm;
-        logsig_pair(sgn * z, ls, sm);
-        if (in) rowsum += ls;
-        d[q] = in ? cm * sgn * sm : 0.0f;
-        cs[q] = d[q];
+        for (int q = 0; q < 16; ++q) {
+          const bool in = mvalid && nb + q < g.N;
+          const float z = v[q] + bias_s[lb + q];
+          const float sgn = (neg[c] >> q) & 1u ? -1.0f : 1.0f;
+          float ls, sm;
+          logsig_pair(sgn * z, ls, sm);
+          if (in) rowsum += ls;
+          d[q] = in ? cm * sgn * sm : 0.0f;
+          cs[q] = d[q];
+        }
+      } else {  // log pi only
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float x = ((neg[c] >> q) & 1u ? -1.0f : 1.0f) * (v[q] + bias_s[lb + q]);
+          if (mvalid && nb + q < g.N) rowsum += fminf(x, 0.0f) - log1pf(expf(-fabsf(x)));
+        }
       }
       if (g.coef) {
         if (full) {

@@ -358,11 +358,11 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
     hsh = fnv1a(hsh, inst->alpha, (size_t)n * 4);
     c->tim_rows = tim_chunk_rows(Bmax, n);
     const size_t rows = (size_t)c->tim_rows;
-    VQ_ALLOC(c->tim_Sx, rows * c->np * esize(c));
+    VQ_ALLOC(c->tim_A, (size_t)Bmax * c->hp * 4);
     VQ_ALLOC(c->tim_S8, rows * c->np);
     VQ_ALLOC(c->tim_H, rows * c->hp * esize(c));
-    VQ_ALLOC(c->tim_row_part, (size_t)((n + 127) / 128) * rows * 4);
-    VQ_ALLOC(c->tim_lp, (size_t)Bmax * (n + 1) * 4);
+    c->tim_ld = ((long long)Bmax * (n + 1) + 3) / 4 * 4;
+    VQ_ALLOC(c->tim_row_part, (size_t)((n + 127) / 128) * (size_t)c->tim_ld * 4);
   }
   c->inst_hash = hsh;
   if (launch_refresh_weights(c, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
@@ -381,8 +381,8 @@ void vqmc_destroy(vqmc_ctx* c) {
   void* ptrs[] = {c->theta, c->adam_m, c->adam_v, c->grad, c->wt_s, c->v_s, c->w_s, c->vt_s, c->row_ptr,
                   c->col, c->w, c->field, c->J, c->J_hi, c->J_lo, c->S, c->E, c->Sx, c->St, c->H, c->Ht,
                   c->D, c->Dt, c->GAt, c->logp, c->coef, c->stats, c->row_part, c->col_part, c->err,
-                  c->step_stats, c->Sbits, c->eloc_part, c->eloc_slice, c->erow, c->alpha, c->tim_Sx,
-                  c->tim_S8, c->tim_H, c->tim_row_part, c->tim_lp};
+                  c->step_stats, c->Sbits, c->eloc_part, c->eloc_slice, c->erow, c->alpha, c->tim_A,
+                  c->tim_S8, c->tim_H, c->tim_row_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
