@@ -318,6 +318,32 @@ def vqmc_grad(params, inst, S, act=RELU):
     return logprob_grad(params, S, coef, act), st, E
 
 
+def per_sample_grads(params, S, act=RELU) -> np.ndarray:
+    """O[b] = grad_theta log pi(s_b) in the flat theta layout, (B, d) FP64:
+    the chain-rule gradient of one sample at a time."""
+    W1, b1, W2, b2 = _made(params)
+    S = _i8(S).reshape(-1, W1.shape[1])
+    rows = [made_to_theta(*logprob_grad(params, S[b:b + 1], np.ones(1), act)) for b in range(S.shape[0])]
+    return np.stack(rows)
+
+
+def sr_direction(params, inst, S, lam, act=RELU):
+    """Stochastic reconfiguration (Sec. 2.1): with the batch estimates of the
+    paper's population forms,
+        g = (1/B) sum_b (E_b - mean E) O_b,   I = (1/B) sum_b O_b O_b^T,
+    the natural-gradient direction solves (I + lam 1) delta = g; the update
+    is theta <- theta - lr delta.  The d x d matrix is formed and solved
+    directly (FP64), so this is for small models.  Returns (delta, stats)."""
+    E = local_energy(params, inst, S, act)
+    st, coef = stats(E)
+    O = per_sample_grads(params, S, act)
+    B, d = O.shape
+    g = O.T @ (E - st[0]) / B
+    I = O.T @ O / B
+    delta = np.linalg.solve(I + lam * np.eye(d), g)
+    return delta, st
+
+
 def adam(theta, m, v, g, t, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
     """In-place Adam step on FP64 arrays."""
     lib = _load()
