@@ -246,6 +246,42 @@ vqmc_status vqmc_adam(vqmc_ctx* ctx, const float* d_grad, vqmc_stream stream);
  * reading; use pinned memory for a truly asynchronous copy). */
 vqmc_status vqmc_step(vqmc_ctx* ctx, int32_t B, vqmc_stream stream, vqmc_step_stats* h_out);
 
+/* Stochastic reconfiguration (natural gradient, Sec. 2.1; the paper's
+ * "SGD+SR" optimiser of Sec. 5.1 with lambda = 1e-3 and lr = 0.1).  With
+ * O_b = grad_theta log pi(s_b) the batch estimates of the paper's gradient
+ * and Fisher forms are g = (1/B) sum_b (E_b - mean E) O_b and
+ * I = (1/B) sum_b O_b O_b^T; the direction delta solves
+ * (I + lambda 1) delta = g.  The d x d matrix is never formed: the library
+ * builds the B x B Gram matrix O O^T from the MADE structure, factors
+ * O O^T / B + lambda by Cholesky (FP32) and returns delta = O^T x.
+ *
+ * These calls need an FP32 context (VQMC_PREC_FP32): with BF16 the
+ * per-sample operands are rounded to bfloat16, which would perturb the Gram
+ * matrix by 2^-9 relative, amplified by its condition number.  They return
+ * UNSUPPORTED for a BF16 context and for B > 16384.  The first SR call on a
+ * context allocates its workspace of about 4 max_batch^2 bytes (padded to a
+ * multiple of 64) with cudaMalloc and synchronises the device; later calls
+ * allocate nothing.  A non-positive Cholesky pivot (only possible through
+ * rounding or non-finite inputs) sets VQMC_DEVERR_NONFINITE. */
+
+/* d_gram float32 [B][B] (row-major, both triangles) = O O^T of the B
+ * configurations d_s int8 [B][n]. */
+vqmc_status vqmc_sr_gram(vqmc_ctx* ctx, int32_t B, const int8_t* d_s, float* d_gram, vqmc_stream stream);
+
+/* d_delta float32 [d] (theta layout) = the SR direction of the batch
+ * (d_s int8 [B][n], energies d_e int32/float32 [B] per instance kind) with
+ * regulariser lambda > 0 (INVALID_ARG otherwise); d_stats (NULL allowed):
+ * the FP64 energy statistics as in vqmc_energy_stats.  B = 0 writes zeros. */
+vqmc_status vqmc_sr_direction(vqmc_ctx* ctx, int32_t B, const int8_t* d_s, const void* d_e, float lambda,
+                              float* d_delta, double* d_stats, vqmc_stream stream);
+
+/* One SGD+SR iteration: B samples with the internal uniforms of the
+ * iteration counter, local energies, FP64 statistics, the SR direction and
+ * theta <- theta - lr delta (the Adam state is untouched); then increments
+ * the iteration counter.  h_out as in vqmc_step. */
+vqmc_status vqmc_sr_step(vqmc_ctx* ctx, int32_t B, float lr, float lambda, vqmc_stream stream,
+                         vqmc_step_stats* h_out);
+
 /* A batch of independent problems (each member an ordinary context with its
  * own model, instance, optimiser and workspaces), stepped together: many
  * Max-Cut instances of different sizes trained at once, so that small

@@ -327,6 +327,13 @@ def per_sample_grads(params, S, act=RELU) -> np.ndarray:
     return np.stack(rows)
 
 
+def sr_gram(params, S, act=RELU) -> np.ndarray:
+    """G[b][c] = O_b . O_c, the (B, B) Gram matrix of the per-sample score
+    vectors (Sec. 2.1): B I with I the batch estimate of the Fisher form."""
+    O = per_sample_grads(params, S, act)
+    return O @ O.T
+
+
 def sr_direction(params, inst, S, lam, act=RELU):
     """Stochastic reconfiguration (Sec. 2.1): with the batch estimates of the
     paper's population forms,

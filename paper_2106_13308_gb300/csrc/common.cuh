@@ -134,6 +134,12 @@ struct vqmc_ctx {
   int64_t launches = 0;
   cudaEvent_t* events = nullptr;  // kMaxTimedSteps * (VQMC_NUM_PARTS + 1)
   vqmc_step_stats* step_stats = nullptr;  // device copy of the last step's stats
+  // stochastic reconfiguration, allocated by the first SR call: the
+  // Cholesky workspace [sr_ld][sr_ld] (lower triangle), its solution and a
+  // vector of ones [sr_ld] (unit coefficients of the per-sample pass)
+  float* sr_A = nullptr;
+  float* sr_x = nullptr;
+  float* sr_ones = nullptr;
 };
 
 namespace vqmc {
@@ -195,6 +201,23 @@ vqmc_status set_last_error(vqmc_status s, const std::string& msg);
 
 // ---- noalloc.cu: scratch bytes vqmc_logprob_noalloc needs for B samples
 size_t noalloc_scratch_bytes(const vqmc_ctx* c, int B);
+
+// ---- sr.cu: stochastic reconfiguration (Gram matrix of the per-sample
+// score vectors, Cholesky solve, SGD step)
+constexpr int kSrMaxBatch = 16384;
+int sr_blocks(int B);
+int sr_ld(const vqmc_ctx* c);
+// allocates the context's SR workspace on first use (synchronous)
+cudaError_t sr_workspace(vqmc_ctx* c);
+// out[b][c] = scale (O O^T)[b][c] + shift [b == c] from the per-sample
+// operands St, Dt, Ht, GAt (unit coefficients); lower triangle, plus the
+// upper if mirror; rows/columns [B, pad_to) of out set to the identity
+cudaError_t launch_sr_gram(const vqmc_ctx* c, int B, float* out, int ldo, float scale, float shift, bool mirror,
+                           int pad_to, cudaStream_t st);
+// factors sr_A (B x B plus identity padding) in place and solves for x
+cudaError_t launch_sr_solve(const vqmc_ctx* c, int B, const float* rhs, float* x, cudaStream_t st, int* launches);
+// theta -= lr delta
+cudaError_t launch_sgd(vqmc_ctx* c, const float* delta, float lr, cudaStream_t st);
 
 // ---- adam.cu
 cudaError_t launch_mask_params(vqmc_ctx* c, cudaStream_t st);

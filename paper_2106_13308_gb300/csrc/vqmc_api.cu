@@ -382,7 +382,7 @@ void vqmc_destroy(vqmc_ctx* c) {
                   c->col, c->w, c->field, c->J, c->J_hi, c->J_lo, c->S, c->E, c->Sx, c->St, c->H, c->Ht,
                   c->D, c->Dt, c->GAt, c->logp, c->coef, c->stats, c->row_part, c->col_part, c->err,
                   c->step_stats, c->Sbits, c->eloc_part, c->eloc_slice, c->erow, c->alpha, c->tim_A,
-                  c->tim_S8, c->tim_H, c->tim_row_part};
+                  c->tim_S8, c->tim_H, c->tim_row_part, c->sr_A, c->sr_x, c->sr_ones};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -588,6 +588,93 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
     const int energy = !sparse ? 2 : (tc ? 0 : 1) + 1 + (c->eloc_slices > 1 ? 1 : 0);
     c->launches += sampler + energy + tim_launches + 1 + 7 + (fuse ? 1 : 2) + (tc ? 2 : 0) + 1;
   }
+  c->iter += 1;
+  return VQMC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------- stochastic reconfiguration
+
+namespace {
+
+vqmc_status sr_check(vqmc_ctx* c, int B) {
+  vqmc_status s = check_B(c, B);
+  if (s != VQMC_OK) return s;
+  if (c->prec != VQMC_PREC_FP32)
+    return fail(VQMC_ERR_UNSUPPORTED, "stochastic reconfiguration needs an FP32 context");
+  if (B > kSrMaxBatch) return fail(VQMC_ERR_UNSUPPORTED, "stochastic reconfiguration supports B <= 16384");
+  VQ_CUDA(sr_workspace(c));
+  return VQMC_OK;
+}
+
+// The adjoint pass's operands with unit coefficients: St, Dt, Ht, GAt hold
+// each sample's s, delta, H and GA (Sec. 2.3 chain rule).
+vqmc_status sr_operands(vqmc_ctx* c, int B, const int8_t* d_s, cudaStream_t st) {
+  VQ_CUDA(launch_spins_to_operands(c, B, d_s, c->Sx, c->St, st));
+  VQ_CUDA(launch_gemm(c, kOpHidden, B, d_s, nullptr, nullptr, st));
+  VQ_CUDA(launch_gemm(c, kOpOut, B, d_s, c->sr_ones, nullptr, st));
+  VQ_CUDA(launch_gemm(c, kOpGA, B, d_s, nullptr, nullptr, st));
+  return VQMC_OK;
+}
+
+// delta = O^T x with (O O^T / B + lambda) x = (E - mean)/B (Sec. 2.1)
+vqmc_status sr_direction(vqmc_ctx* c, int B, const int8_t* d_s, const void* d_e, float lambda, float* d_delta,
+                         double* d_stats, cudaStream_t st) {
+  VQ_CUDA(launch_stats(c, B, d_e, d_stats, c->coef, st));
+  vqmc_status s = sr_operands(c, B, d_s, st);
+  if (s != VQMC_OK) return s;
+  VQ_CUDA(launch_sr_gram(c, B, c->sr_A, sr_ld(c), 1.0f / (float)B, lambda, false, sr_blocks(B) * 64, st));
+  VQ_CUDA(launch_sr_solve(c, B, c->coef, c->sr_x, st, nullptr));
+  return backward_from_operands(c, B, d_s, c->sr_x, d_delta, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+vqmc_status vqmc_sr_gram(vqmc_ctx* c, int32_t B, const int8_t* d_s, float* d_gram, vqmc_stream stream) {
+  vqmc_status s = sr_check(c, B);
+  if (s != VQMC_OK) return s;
+  if (B == 0) return VQMC_OK;
+  if (!d_s || !d_gram) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  s = sr_operands(c, B, d_s, S(stream));
+  if (s != VQMC_OK) return s;
+  VQ_CUDA(launch_sr_gram(c, B, d_gram, B, 1.0f, 0.0f, true, 0, S(stream)));
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_sr_direction(vqmc_ctx* c, int32_t B, const int8_t* d_s, const void* d_e, float lambda,
+                              float* d_delta, double* d_stats, vqmc_stream stream) {
+  vqmc_status s = sr_check(c, B);
+  if (s != VQMC_OK) return s;
+  if (!(lambda > 0.0f) || !std::isfinite(lambda)) return fail(VQMC_ERR_INVALID_ARG, "lambda must be finite and > 0");
+  if (!d_delta) return fail(VQMC_ERR_INVALID_ARG, "null direction");
+  if (B == 0) {
+    VQ_CUDA(cudaMemsetAsync(d_delta, 0, c->d * 4, S(stream)));
+    return VQMC_OK;
+  }
+  if (!d_s || !d_e) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  return sr_direction(c, B, d_s, d_e, lambda, d_delta, d_stats ? d_stats : c->stats, S(stream));
+}
+
+vqmc_status vqmc_sr_step(vqmc_ctx* c, int32_t B, float lr, float lambda, vqmc_stream stream, vqmc_step_stats* h_out) {
+  vqmc_status s = sr_check(c, B);
+  if (s != VQMC_OK) return s;
+  if (B == 0) return fail(VQMC_ERR_INVALID_ARG, "vqmc_sr_step needs B >= 1");
+  if (!(lambda > 0.0f) || !std::isfinite(lambda)) return fail(VQMC_ERR_INVALID_ARG, "lambda must be finite and > 0");
+  if (!std::isfinite(lr)) return fail(VQMC_ERR_INVALID_ARG, "lr must be finite");
+  cudaStream_t st = S(stream);
+  VQ_CUDA(launch_sampler(c, B, nullptr, c->iter, c->S, nullptr, st));
+  s = vqmc_local_energy(c, B, c->S, c->E, stream);
+  if (s != VQMC_OK) return s;
+  s = sr_direction(c, B, c->S, c->E, lambda, c->grad, c->stats, st);
+  if (s != VQMC_OK) return s;
+  VQ_CUDA(launch_sgd(c, c->grad, lr, st));
+  VQ_CUDA(launch_refresh_weights(c, st));
+  fill_step_stats<<<1, 1, 0, st>>>(c->stats, c->iter, c->err, c->step_stats);
+  VQ_CUDA(cudaGetLastError());
+  if (h_out) VQ_CUDA(cudaMemcpyAsync(h_out, c->step_stats, sizeof(vqmc_step_stats), cudaMemcpyDeviceToHost, st));
   c->iter += 1;
   return VQMC_OK;
 }

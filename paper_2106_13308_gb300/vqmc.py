@@ -36,7 +36,8 @@ EXPORTS = [
     "vqmc_logprob", "vqmc_logprob_backward", "vqmc_energy_stats", "vqmc_grad", "vqmc_adam", "vqmc_step",
     "vqmc_last_batch", "vqmc_iteration", "vqmc_check", "vqmc_save", "vqmc_load", "vqmc_timing_enable",
     "vqmc_timing_read", "vqmc_logprob_noalloc", "vqmc_last_error", "vqmc_batch_create", "vqmc_batch_destroy",
-    "vqmc_batch_count", "vqmc_batch_member", "vqmc_batch_step",
+    "vqmc_batch_count", "vqmc_batch_member", "vqmc_batch_step", "vqmc_sr_gram", "vqmc_sr_direction",
+    "vqmc_sr_step",
 ]
 PARTS = ["sample", "energy", "stats", "grad", "adam"]
 
@@ -111,6 +112,9 @@ def load_library(path: str = LIB_PATH):
         "vqmc_batch_count": (I32, [P]),
         "vqmc_batch_member": (P, [P, I32]),
         "vqmc_batch_step": (st, [P, ctypes.POINTER(I32), P, ctypes.POINTER(StepStats)]),
+        "vqmc_sr_gram": (st, [P, I32, P, P, P]),
+        "vqmc_sr_direction": (st, [P, I32, P, P, ctypes.c_float, P, P, P]),
+        "vqmc_sr_step": (st, [P, I32, ctypes.c_float, ctypes.c_float, P, ctypes.POINTER(StepStats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -213,6 +217,20 @@ def vqmc_adam(ctx, grad, stream=None):
 
 def vqmc_step(ctx, B: int, out: StepStats | None = None, stream=None):
     _check(load_library().vqmc_step(ctx, B, _stream(stream), ctypes.byref(out) if out is not None else None))
+
+
+def vqmc_sr_gram(ctx, B: int, s, gram, stream=None):
+    _check(load_library().vqmc_sr_gram(ctx, B, _ptr(s), _ptr(gram), _stream(stream)))
+
+
+def vqmc_sr_direction(ctx, B: int, s, e, lam: float, delta, stats=None, stream=None):
+    _check(load_library().vqmc_sr_direction(ctx, B, _ptr(s), _ptr(e), float(lam), _ptr(delta), _ptr(stats),
+                                            _stream(stream)))
+
+
+def vqmc_sr_step(ctx, B: int, lr: float, lam: float, out: StepStats | None = None, stream=None):
+    _check(load_library().vqmc_sr_step(ctx, B, float(lr), float(lam), _stream(stream),
+                                       ctypes.byref(out) if out is not None else None))
 
 
 def vqmc_check(ctx) -> int:
@@ -374,6 +392,23 @@ class VQMC:
 
     def step(self, B, out: StepStats | None = None):
         vqmc_step(self.ctx, B, out)
+        return out
+
+    # stochastic reconfiguration (FP32 contexts)
+    def sr_gram(self, s):
+        B = s.shape[0]
+        G = torch.empty((B, B), dtype=torch.float32, device="cuda")
+        vqmc_sr_gram(self.ctx, B, s, G)
+        return G
+
+    def sr_direction(self, s, e, lam=1e-3):
+        delta = torch.empty(self.d, dtype=torch.float32, device="cuda")
+        stats = torch.empty(4, dtype=torch.float64, device="cuda")
+        vqmc_sr_direction(self.ctx, s.shape[0], s, e, lam, delta, stats)
+        return delta, stats
+
+    def sr_step(self, B, lr=0.1, lam=1e-3, out: StepStats | None = None):
+        vqmc_sr_step(self.ctx, B, lr, lam, out)
         return out
 
     def last_batch(self, B):

@@ -54,3 +54,45 @@ def test_sr_direction_solves_the_regularised_system_and_tends_to_the_gradient():
     lam = 1e8
     delta, _ = oracle.sr_direction(P, inst, S, lam, act)
     assert np.allclose(lam * delta, g, rtol=1e-5, atol=1e-12)
+
+
+def test_per_sample_gradient_against_central_differences():
+    """O[b] against central differences of log pi(s_b) (FP64, eps = 1e-6) on
+    random parameters of every block (sigmoid hidden units: no kinks)."""
+    n, h = 9, 7
+    theta = inputs.lively_params(n, h, 21).astype(np.float64)
+    S = inputs.spins(5, n, 22)
+    act = oracle.SIGMOID
+    P = oracle.theta_to_made(theta, n, h)
+    deg = oracle.degrees(n, h)
+    O = oracle.per_sample_grads(P, S, act)
+    rng = np.random.default_rng(23)
+    d = theta.size
+    eps = 1e-6
+    for p in rng.choice(d, 40, replace=False):
+        tp, tm = theta.copy(), theta.copy()
+        tp[p] += eps
+        tm[p] -= eps
+        fd = (oracle.logprob(oracle.theta_to_made(tp, n, h), S, act)
+              - oracle.logprob(oracle.theta_to_made(tm, n, h), S, act)) / (2 * eps)
+        # entries outside the MADE masks are not parameters of the model
+        if p < n * h:
+            j, k = divmod(p, h)
+            if not deg[k] >= j + 1:
+                assert np.all(O[:, p] == 0)
+                continue
+        elif n * h + h <= p < 2 * n * h + h:
+            i, k = divmod(p - n * h - h, h)
+            if not i + 1 > deg[k]:
+                assert np.all(O[:, p] == 0)
+                continue
+        assert np.allclose(O[:, p], fd, rtol=1e-6, atol=1e-8)
+
+
+def test_sr_gram_is_the_matrix_of_inner_products():
+    inst, P, S, act = _case()
+    O = oracle.per_sample_grads(P, S, act)
+    G = oracle.sr_gram(P, S, act)
+    assert np.allclose(G, G.T, rtol=0, atol=0)
+    assert np.allclose(np.diag(G), (O * O).sum(axis=1), rtol=1e-12)
+    assert np.linalg.eigvalsh(G).min() > -1e-9 * np.abs(G).max()
