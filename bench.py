@@ -17,6 +17,19 @@ size (n = 500, h = 5 (ln n)^2 = 193, B = 1024; Tables 1 and 2), is timed the
 same way and reported under "tim": its local energy adds the off-diagonal
 part, n + 1 log-prob evaluations per sample through the tensor-core GEMMs.
 
+A third, stochastic reconfiguration (the paper's SGD+SR optimiser, Sec. 2.1 and
+5.1: lambda = 1e-3, lr = 0.1) on the same TIM workload in FP32, is reported
+under "sr": its iteration adds the B x B Gram matrix of the per-sample score
+vectors, a Cholesky solve and a second adjoint pass.  --sr-only runs this arm
+alone (the command the SR profiles were taken with).
+
+A fourth, many independent instances trained together: 64 Max-Cut instances of
+uneven size (n ~ U{100..5000}, G(n, 6/(n-1)), weights +-1, 512 samples each,
+hidden units min(n, 2048): the samplers hold at most 2048), BF16, stepped as
+one CUDA graph launch per batched iteration under the schedule the library's
+autotuner picked; reported under "batched" beside the same batch stepped call
+by call.
+
 --impl reference times the FP64 CPU oracle on the host cores instead (a
 bounded sub-batch per step, scaled linearly to the full batch).
 """
@@ -203,6 +216,127 @@ def _timed_steps(m, B, K, W, dist_on):
     return ms, parts, steps, launches
 
 
+def _sr_arm(K, W, dist_on, world):
+    """SGD+SR iterations (vqmc_sr_step) on the TIM workload in FP32, with the
+    library's per-part times; the Gram kernel's work over the time of a
+    vqmc_sr_gram call (per-sample operands + Gram matrix) is a lower bound
+    on the Gram kernel's own rate."""
+    import torch
+    from paper_2106_13308_gb300 import inputs
+    cfg, inst = _workload(TIM_WORKLOAD)
+    B, n, h = cfg["B"], cfg["n"], cfg["h"]
+    m = _make(cfg, inst, "fp32")
+    lr, lam = 0.1, 1e-3
+    stream = torch.cuda.current_stream()
+    for _ in range(W):
+        m.sr_step(B, lr, lam)
+    torch.cuda.synchronize()
+    m.timing_enable(True)
+    if dist_on:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        m.sr_step(B, lr, lam)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist_on:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    parts, steps, launches = m.timing_read()
+    m.timing_enable(False)
+    ms, val = _replica_rate(ms, K, world, "cuda")
+    # the Gram call alone, on the last step's samples
+    s, _ = m.last_batch(B)
+    s = s.clone()
+    for _ in range(2):
+        m.sr_gram(s)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(K):
+        m.sr_gram(s)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    gram_ms = g0.elapsed_time(g1) / K
+    gflop = 5.0 * (n + h) * B * (B + 1) / 2
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    ach = gflop / (gram_ms / 1000.0) / 1e12
+    out = {"workload": f"{TIM_WORKLOAD} in FP32: transverse-field Ising, n={n}, MADE h={h} {cfg['act']}, "
+                       f"batch {B}; SGD+SR with lambda={lam}, lr={lr} (Sec. 5.1)",
+           "value": val, "unit": UNIT, "ms_per_step": ms / K, "samples_per_s": val * B, "steps": K,
+           "part_ms": {k: v / max(steps, 1) for k, v in parts.items()}, "gpu_launches": launches,
+           "gram_call_ms": gram_ms,
+           "roofline_gram": {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                             "frac": ach / fp32_peak,
+                             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                             "algorithmic": f"5*(n+h)*B*(B+1)/2 = {gflop:.3e} flop per Gram matrix; timed over "
+                                            "the whole vqmc_sr_gram call (operand GEMMs included), so a lower "
+                                            "bound on the kernel's own rate"},
+           "device_error_flags": m.check()}
+    del m
+    return out
+
+
+def _batched_arm(K, W, dist_on, world):
+    """64 instances of uneven size in one batch: autotuned schedule, one graph
+    launch per batched iteration, against eager vqmc_batch_step calls."""
+    import torch
+    from paper_2106_13308_gb300 import inputs
+    from paper_2106_13308_gb300.vqmc import VQMCBatch
+    cfgs = inputs.batched_configs()
+    probs = [dict(n=c["n"], h=min(c["h"], 2048), max_batch=c["B"], instance=inputs.make_instance(c), act=c["act"],
+                  precision="bf16", seed=c["graph_seed"]) for c in cfgs]
+    Bs = [p["max_batch"] for p in probs]
+    batch = VQMCBatch(probs)
+    for m, c, p in zip(batch.members, cfgs, probs):
+        m.set_params(torch.from_numpy(inputs.made_params(c["n"], p["h"], c["param_seed"], w_std=c["w_std"])))
+    stream = torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        streams, tuned_ms = batch.autotune(Bs)
+        tune_s = time.perf_counter() - t0
+        # eager batched iterations (default schedule is replaced by the tuned one;
+        # the eager arm uses it too, so the difference is the launch path)
+        for _ in range(W):
+            batch.step(Bs)
+        stream.synchronize()
+        if dist_on:
+            torch.distributed.barrier()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(K):
+            batch.step(Bs)
+        e1.record(stream)
+        stream.synchronize()
+        eager_ms = e0.elapsed_time(e1) / K
+        for _ in range(W):
+            batch.graph_launch()
+        stream.synchronize()
+        if dist_on:
+            torch.distributed.barrier()
+        g0, g1 = ev(), ev()
+        g0.record(stream)
+        for _ in range(K):
+            batch.graph_launch()
+        g1.record(stream)
+        stream.synchronize()
+        graph_ms_total = g0.elapsed_time(g1)
+    flags = [m.check() for m in batch.members]
+    graph_ms, val = _replica_rate(graph_ms_total, K, world, "cuda")
+    ns = [c["n"] for c in cfgs]
+    out = {"workload": f"{len(cfgs)} Max-Cut instances, n ~ U{{100..5000}} (min {min(ns)}, max {max(ns)}), "
+                       "G(n, 6/(n-1)), weights +-1, MADE h = min(n, 2048) relu, 512 samples each, BF16, Adam",
+           "value": val, "unit": "batched it/s", "ms_per_step": graph_ms / K,
+           "samples_per_s": val * sum(Bs), "steps": K,
+           "eager_ms_per_step": eager_ms, "autotuned_streams": streams, "autotune_ms_per_step": tuned_ms,
+           "autotune_wall_s": tune_s, "device_error_flags": int(any(flags))}
+    batch.close()
+    return out
+
+
 def _e2e(m, B, K, W):
     """Same metric through the public Python API as a user runs it: every step
     reads the statistics and the batch's energies back to pinned host memory."""
@@ -282,6 +416,10 @@ def main():
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tim", action="store_true", help="skip the transverse-field Ising workload")
+    ap.add_argument("--no-sr", action="store_true", help="skip the stochastic reconfiguration arm")
+    ap.add_argument("--sr-only", action="store_true", help="run only the stochastic reconfiguration arm")
+    ap.add_argument("--no-batched", action="store_true", help="skip the many-instances arm")
+    ap.add_argument("--batched-only", action="store_true", help="run only the many-instances arm")
     args = ap.parse_args()
     rank, world, local = _dist_env()
     W = max(args.warmup, 3)
@@ -329,6 +467,13 @@ def main():
     torch.cuda.set_device(local)
     import __graft_entry__
     __graft_entry__.build()
+    if args.sr_only or args.batched_only:
+        res = {"sr": _sr_arm(K, W, dist_on, world)} if args.sr_only else {"batched": _batched_arm(K, W, dist_on, world)}
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        if dist_on:
+            torch.distributed.destroy_process_group()
+        return
     cfg, inst = _workload(args.config)
     B = cfg["B"]
 
@@ -401,6 +546,16 @@ def main():
                "device_error_flags": mt.check()}
         del mt
 
+    sr = None
+    if not args.no_sr:
+        torch.cuda.empty_cache()
+        sr = _sr_arm(max(3, K // 2), W, dist_on, world)
+
+    batched = None
+    if not args.no_batched:
+        torch.cuda.empty_cache()
+        batched = _batched_arm(max(3, K // 4), W, dist_on, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = _cpu_baseline(cfg, inst)
@@ -413,7 +568,7 @@ def main():
                 "samples_per_s": value * B,
                 # exact samples per second of the sampler alone (uniforms are drawn inside it)
                 "sampler_samples_per_s": world * B / (sample_ms / 1000.0),
-                "part_ms": part_ms, "fp32": fp32, "tim": tim,
+                "part_ms": part_ms, "fp32": fp32, "tim": tim, "sr": sr, "batched": batched,
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clk, "device_error_flags": flags}

@@ -278,9 +278,33 @@ vqmc_status vqmc_sr_direction(vqmc_ctx* ctx, int32_t B, const int8_t* d_s, const
 /* One SGD+SR iteration: B samples with the internal uniforms of the
  * iteration counter, local energies, FP64 statistics, the SR direction and
  * theta <- theta - lr delta (the Adam state is untouched); then increments
- * the iteration counter.  h_out as in vqmc_step. */
+ * the iteration counter.  h_out as in vqmc_step.  While timing is enabled
+ * (vqmc_timing_enable) it records the parts of vqmc_step, with GRAD = the SR
+ * direction (per-sample operands, Gram matrix, Cholesky, solves, adjoint)
+ * and ADAM = the SGD step with the weight-copy refresh. */
 vqmc_status vqmc_sr_step(vqmc_ctx* ctx, int32_t B, float lr, float lambda, vqmc_stream stream,
                          vqmc_step_stats* h_out);
+
+/* Captured iterations.  The kernels of an iteration read the Philox
+ * iteration counter and the Adam step factors from device memory that the
+ * iteration itself advances, so a CUDA graph of `steps` consecutive
+ * iterations can be replayed for the iterations that follow, each replay
+ * giving exactly what the same number of vqmc_step (optimizer
+ * VQMC_OPT_ADAM) or vqmc_sr_step (VQMC_OPT_SR, with sr_lr and sr_lambda)
+ * calls would.  Capturing runs nothing and leaves the counters unchanged; it
+ * replaces any earlier graph of the context.  `stream` must not be the
+ * legacy default stream (NULL).  SR graphs need an FP32 context; their
+ * workspace is allocated before the capture.  Errors: those of the captured
+ * call, INVALID_ARG, CUDA (capture or instantiation failed). */
+enum { VQMC_OPT_ADAM = 0, VQMC_OPT_SR = 1 };
+vqmc_status vqmc_graph_capture(vqmc_ctx* ctx, int32_t B, int32_t steps, int32_t optimizer, float sr_lr,
+                               float sr_lambda, vqmc_stream stream);
+
+/* Launches the captured iterations on `stream` (one graph launch) and
+ * advances the context's counters by their number; h_out (NULL allowed)
+ * receives the last iteration's statistics as in vqmc_step.  INVALID_ARG if
+ * nothing was captured. */
+vqmc_status vqmc_graph_launch(vqmc_ctx* ctx, vqmc_stream stream, vqmc_step_stats* h_out);
 
 /* A batch of independent problems (each member an ordinary context with its
  * own model, instance, optimiser and workspaces), stepped together: many
@@ -313,6 +337,29 @@ vqmc_ctx* vqmc_batch_member(vqmc_batch* batch, int32_t i);
  * statistics.  Errors: those of vqmc_step, for the first member that fails
  * (the members before it have stepped), or INVALID_ARG for a NULL argument. */
 vqmc_status vqmc_batch_step(vqmc_batch* batch, const int32_t* B, vqmc_stream stream, vqmc_step_stats* h_out);
+
+/* Captures `steps` consecutive vqmc_batch_step calls (member i with B[i]
+ * samples, the batch's current schedule) as one CUDA graph owned by the
+ * batch, replacing any earlier one; as vqmc_graph_capture for one context
+ * (runs nothing, counters unchanged, a non-default stream). */
+vqmc_status vqmc_batch_graph_capture(vqmc_batch* batch, const int32_t* B, int32_t steps, vqmc_stream stream);
+
+/* One graph launch of the captured batched iterations; every member's
+ * counters advance by their number.  h_out: NULL or `count` records. */
+vqmc_status vqmc_batch_graph_launch(vqmc_batch* batch, vqmc_stream stream, vqmc_step_stats* h_out);
+
+/* Autotuner of the batch's schedule: measures one iteration of each member
+ * alone, then times one captured batched iteration (graph replays) under
+ * each candidate schedule -- 1, 2, 4, ... up to the batch's internal streams,
+ * with members assigned round-robin in index order or longest first onto
+ * the least-loaded stream -- and keeps the fastest schedule, with its
+ * captured graph (one iteration, for vqmc_batch_graph_launch).  The
+ * iterations it times are ordinary iterations of every member: each member
+ * advances by 2 + 4 x (number of candidates) iterations.  streams_out and
+ * ms_out (NULL allowed) receive the chosen number of streams and its device
+ * time per batched iteration.  `stream`: not the legacy default stream. */
+vqmc_status vqmc_batch_autotune(vqmc_batch* batch, const int32_t* B, vqmc_stream stream, int32_t* streams_out,
+                                double* ms_out);
 
 /* Device pointers to the last vqmc_step's samples (int8 [B][n]) and energies
  * (int32/float32 [B]); owned by the context, overwritten by the next step. */

@@ -91,13 +91,14 @@ template <typename T>
 __global__ void __launch_bounds__(256) adam_refresh_kernel(int n, int h, int hp, int np, float* __restrict__ theta,
                                                            float* __restrict__ m, float* __restrict__ v,
                                                            const float* __restrict__ g, float lr, float b1, float b2,
-                                                           float inv_bc1, float inv_bc2, float eps, T* __restrict__ wt_s,
+                                                           const float* __restrict__ ibc, float eps, T* __restrict__ wt_s,
                                                            T* __restrict__ v_s, T* __restrict__ w_s,
                                                            T* __restrict__ vt_s) {
   __shared__ float tile[32][33];
   const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32, z = blockIdx.z;
   const int tx = threadIdx.x, ty = threadIdx.y;
   if (tile_masked(z, r0, 32, k0, 32, n, h)) return;
+  const float inv_bc1 = __ldg(ibc), inv_bc2 = __ldg(ibc + 1);
   const long long off = z == 0 ? 0 : (long long)n * h + h;
   for (int rr = ty; rr < 32; rr += 8) {
     const int r = r0 + rr, k = k0 + tx;
@@ -149,13 +150,14 @@ template <typename T>
 __global__ void __launch_bounds__(256) adam_refresh4_kernel(int n, int h, int hp, int np, float* __restrict__ theta,
                                                             float* __restrict__ m, float* __restrict__ v,
                                                             const float* __restrict__ g, float lr, float b1, float b2,
-                                                            float inv_bc1, float inv_bc2, float eps,
+                                                            const float* __restrict__ ibc, float eps,
                                                             T* __restrict__ wt_s, T* __restrict__ v_s,
                                                             T* __restrict__ w_s, T* __restrict__ vt_s) {
   __shared__ float tile[32][129];
   const int k0 = blockIdx.x * 128, r0 = blockIdx.y * 32, z = blockIdx.z;
   const int tx = threadIdx.x, ty = threadIdx.y;
   if (tile_masked(z, r0, 32, k0, 128, n, h)) return;
+  const float inv_bc1 = __ldg(ibc), inv_bc2 = __ldg(ibc + 1);
   const long long off = z == 0 ? 0 : (long long)n * h + h;
   const int k = k0 + 4 * tx;
   float4 G[4], M[4], V[4], TH[4];
@@ -215,12 +217,25 @@ __global__ void l2_prefetch_kernel(const char* __restrict__ p, size_t bytes) {
     asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p + o));
 }
 
+// Next Adam step: t += 1 and its bias corrections.
+__global__ void adam_advance_kernel(DevState* s, float beta1, float beta2) {
+  s->adam_t += 1;
+  adam_factors(s, beta1, beta2);
+}
+
+__global__ void set_state_kernel(DevState* s, unsigned long long iter, long long adam_t, float beta1, float beta2) {
+  s->iter = iter;
+  s->adam_t = adam_t;
+  adam_factors(s, beta1, beta2);
+}
+
 // Adam on the biases b1 (after W1^T) and b2 (after W2).
 __global__ void adam_bias_kernel(int n, int h, float* __restrict__ theta, float* __restrict__ m,
                                  float* __restrict__ v, const float* __restrict__ g, float lr, float b1, float b2,
-                                 float inv_bc1, float inv_bc2, float eps) {
+                                 const float* __restrict__ ibc, float eps) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= h + n) return;
+  const float inv_bc1 = __ldg(ibc), inv_bc2 = __ldg(ibc + 1);
   const long long q = t < h ? (long long)n * h + t : 2ll * n * h + h + (t - h);
   const float gq = g[q];
   const float mq = b1 * m[q] + (1.0f - b1) * gq;
@@ -269,43 +284,47 @@ cudaError_t launch_refresh_weights(vqmc_ctx* c, cudaStream_t st) {
   return c->prec == VQMC_PREC_BF16 ? refresh<bf16>(c, st) : refresh<float>(c, st);
 }
 
-AdamStep adam_advance(vqmc_ctx* c) {
+AdamStep adam_advance(vqmc_ctx* c, cudaStream_t st) {
   c->adam_t += 1;
-  const double t = (double)c->adam_t;
-  const double bc1 = 1.0 - pow((double)c->cfg.beta1, t), bc2 = 1.0 - pow((double)c->cfg.beta2, t);
-  return AdamStep{(float)(1.0 / bc1), (float)(1.0 / bc2)};
+  adam_advance_kernel<<<1, 1, 0, st>>>(c->dstate, c->cfg.beta1, c->cfg.beta2);
+  return AdamStep{&c->dstate->ibc1};
+}
+
+cudaError_t launch_set_state(vqmc_ctx* c, cudaStream_t st) {
+  set_state_kernel<<<1, 1, 0, st>>>(c->dstate, (unsigned long long)c->iter, (long long)c->adam_t, c->cfg.beta1,
+                                    c->cfg.beta2);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_adam_bias(vqmc_ctx* c, const float* d_grad, AdamStep a, cudaStream_t st) {
   adam_bias_kernel<<<(c->h + c->n + 255) / 256, 256, 0, st>>>(c->n, c->h, c->theta, c->adam_m, c->adam_v, d_grad,
-                                                              c->cfg.lr, c->cfg.beta1, c->cfg.beta2, a.ibc1, a.ibc2,
-                                                              c->cfg.eps);
+                                                              c->cfg.lr, c->cfg.beta1, c->cfg.beta2, a.ibc, c->cfg.eps);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adam(vqmc_ctx* c, const float* d_grad, cudaStream_t st) {
-  const AdamStep a = adam_advance(c);
-  const float ib1 = a.ibc1, ib2 = a.ibc2;
+cudaError_t launch_adam(vqmc_ctx* c, const float* d_grad, cudaStream_t st, bool advance) {
+  const AdamStep a = advance ? adam_advance(c, st) : AdamStep{&c->dstate->ibc1};
+  const float* ib = a.ibc;
   const bool vec = c->h % 4 == 0;  // rows of theta start on 16-byte boundaries
   const dim3 grid(vec ? (c->h + 127) / 128 : (c->h + 31) / 32, (c->n + 31) / 32, 2), block(32, 8);
   // the tensor-core sampler reads W1 through w_s; only the CUDA-core one needs wt_s
   const bool need_wt = c->sampler != VQMC_SAMPLER_TENSOR_CORE;
   if (vec && c->prec == VQMC_PREC_BF16)
     adam_refresh4_kernel<bf16><<<grid, block, 0, st>>>(
-        c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib1,
-        ib2, c->cfg.eps, need_wt ? (bf16*)c->wt_s : nullptr, (bf16*)c->v_s, (bf16*)c->w_s, (bf16*)c->vt_s);
+        c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib,
+        c->cfg.eps, need_wt ? (bf16*)c->wt_s : nullptr, (bf16*)c->v_s, (bf16*)c->w_s, (bf16*)c->vt_s);
   else if (vec)
     adam_refresh4_kernel<float><<<grid, block, 0, st>>>(
-        c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib1,
-        ib2, c->cfg.eps, need_wt ? (float*)c->wt_s : nullptr, (float*)c->v_s, (float*)c->w_s, (float*)c->vt_s);
+        c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib,
+        c->cfg.eps, need_wt ? (float*)c->wt_s : nullptr, (float*)c->v_s, (float*)c->w_s, (float*)c->vt_s);
   else if (c->prec == VQMC_PREC_BF16)
     adam_refresh_kernel<bf16><<<grid, block, 0, st>>>(
-        c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib1,
-        ib2, c->cfg.eps, need_wt ? (bf16*)c->wt_s : nullptr, (bf16*)c->v_s, (bf16*)c->w_s, (bf16*)c->vt_s);
+        c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib,
+        c->cfg.eps, need_wt ? (bf16*)c->wt_s : nullptr, (bf16*)c->v_s, (bf16*)c->w_s, (bf16*)c->vt_s);
   else
     adam_refresh_kernel<float><<<grid, block, 0, st>>>(
-        c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib1,
-        ib2, c->cfg.eps, need_wt ? (float*)c->wt_s : nullptr, (float*)c->v_s, (float*)c->w_s, (float*)c->vt_s);
+        c->n, c->h, c->hp, c->np, c->theta, c->adam_m, c->adam_v, d_grad, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, ib,
+        c->cfg.eps, need_wt ? (float*)c->wt_s : nullptr, (float*)c->v_s, (float*)c->w_s, (float*)c->vt_s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_adam_bias(c, d_grad, a, st);

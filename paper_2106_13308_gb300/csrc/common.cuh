@@ -48,6 +48,36 @@ constexpr uint32_t kErrNonfinite = VQMC_DEVERR_NONFINITE;
 // may itself suspend the thread for a hardware-chosen interval).
 constexpr long long kSpinLimit = 1ll << 26;
 
+// Counters of the iteration that the kernels read on the device, so that a
+// captured CUDA graph replays consecutive iterations: the Philox iteration
+// of the next step, the Adam step count and the bias corrections
+// 1 / (1 - beta^t) of the current Adam step.  The context keeps host mirrors
+// (iter, adam_t) that every enqueue advances in step.
+struct DevState {
+  unsigned long long iter;
+  long long adam_t;
+  float ibc1, ibc2;
+};
+
+// beta^t for integer t >= 0 by repeated squaring (a fixed function of t, so a
+// run resumed from a checkpoint reproduces it exactly).
+__device__ __forceinline__ double pow_int(double b, long long t) {
+  double r = 1.0;
+  while (t > 0) {
+    if (t & 1) r *= b;
+    b *= b;
+    t >>= 1;
+  }
+  return r;
+}
+
+// The bias corrections 1 / (1 - beta^t) of Adam step t = s->adam_t (1 for t = 0).
+__device__ __forceinline__ void adam_factors(DevState* s, float beta1, float beta2) {
+  const long long t = s->adam_t;
+  s->ibc1 = t < 1 ? 1.0f : (float)(1.0 / (1.0 - pow_int((double)beta1, t)));
+  s->ibc2 = t < 1 ? 1.0f : (float)(1.0 / (1.0 - pow_int((double)beta2, t)));
+}
+
 }  // namespace vqmc
 
 // The context behind the opaque handle of vqmc.h.
@@ -71,6 +101,12 @@ struct vqmc_ctx {
   float* grad = nullptr;
   int64_t adam_t = 0;
   uint64_t iter = 0;
+  vqmc::DevState* dstate = nullptr;  // device copy of the counters
+  // captured iterations (vqmc_graph_capture): the instantiated graph, its
+  // number of iterations and whether they are Adam steps
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  bool graph_adam = false;
 
   // Kernel-side weight copies, element type float (FP32) or bf16 (BF16):
   //   wt_s [sampler_rows(n)][hp]  row j = column j of W1 (input j, 1-based),
@@ -135,19 +171,25 @@ struct vqmc_ctx {
   cudaEvent_t* events = nullptr;  // kMaxTimedSteps * (VQMC_NUM_PARTS + 1)
   vqmc_step_stats* step_stats = nullptr;  // device copy of the last step's stats
   // stochastic reconfiguration, allocated by the first SR call: the
-  // Cholesky workspace [sr_ld][sr_ld] (lower triangle), its solution and a
-  // vector of ones [sr_ld] (unit coefficients of the per-sample pass)
+  // Cholesky workspace [sr_ld][sr_ld] (lower triangle), its solution, a
+  // vector of ones [sr_ld] (unit coefficients of the per-sample pass), the
+  // inverse-transposed diagonal blocks of the factor [sr_ld / 64][64][64],
+  // and the Gram kernel's event order [n + h]
   float* sr_A = nullptr;
   float* sr_x = nullptr;
   float* sr_ones = nullptr;
+  float* sr_xinv = nullptr;
+  int* sr_events = nullptr;
 };
 
 namespace vqmc {
 
 // ---- sampler.cu
 cudaError_t launch_uniforms(int B, int n, uint64_t seed, uint64_t iteration, float* d_u, cudaStream_t st);
+// it_dev: when not null, the Philox iteration is read from it on the device
+// (the context's DevState) instead of `iteration`
 cudaError_t launch_sampler(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,
-                           float* d_logp, cudaStream_t st);
+                           float* d_logp, cudaStream_t st, const unsigned long long* it_dev = nullptr);
 // ---- adam.cu: the tensor-core sampler's weight copies (v_s, w_s) into L2
 cudaError_t launch_prefetch_sampler_weights(const vqmc_ctx* c, cudaStream_t st);
 // ---- sampler_tc.cu: block size of the tensor-core sampler for this model, 0
@@ -157,7 +199,7 @@ int sampler_tc_block(const vqmc_ctx* c);
 // GEMM operands Sx, St and the packed layout of the sparse energy)
 cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,
                               float* d_logp, cudaStream_t st, void* sx = nullptr, void* stt = nullptr,
-                              uint32_t* sbits = nullptr);
+                              uint32_t* sbits = nullptr, const unsigned long long* it_dev = nullptr);
 
 // ---- eloc.cu
 // packed: c->Sbits already holds the spins (written by the sampler)
@@ -170,8 +212,10 @@ cudaError_t launch_tim_offdiag(const vqmc_ctx* c, int B, const int8_t* d_s, floa
                                int* launches = nullptr);
 // rows per chunk of the flipped states for at most Bmax samples
 int tim_chunk_rows(int Bmax, int n);
+// advance: also start the next Adam step on the device (t += 1 and its
+// factors), saving vqmc_step a launch; the caller advances the host mirror
 cudaError_t launch_stats(const vqmc_ctx* c, int B, const void* d_e, double* d_stats, float* d_coef,
-                         cudaStream_t st);
+                         cudaStream_t st, bool advance = false);
 cudaError_t launch_spins_to_operands(const vqmc_ctx* c, int B, const int8_t* d_s, void* Sx, void* St,
                                      cudaStream_t st);
 cudaError_t launch_row_sum(const vqmc_ctx* c, int B, int ntiles, float* out, cudaStream_t st);
@@ -188,10 +232,11 @@ enum GemmOp {
   kOpDW = 4,      // dW1^T = St . GAt^T (masked) -> grad, or the Adam step on W1^T
   kOpEloc = 5     // T = S J (hi/lo) ; row partials 1/2 s.T
 };
-// Adam factors of one step (1 / (1 - beta^t) of both moments) for the
-// weight-gradient GEMMs that apply the step in their epilogue.
+// Adam factors of one step for the weight-gradient GEMMs that apply the step
+// in their epilogue: device pointer to {1 / (1 - beta1^t), 1 / (1 - beta2^t)}
+// (the context's DevState).
 struct AdamStep {
-  float ibc1, ibc2;
+  const float* ibc;
 };
 cudaError_t launch_gemm(const vqmc_ctx* c, GemmOp op, int B, const int8_t* d_s, const float* coef,
                         float* grad, cudaStream_t st, const AdamStep* fuse = nullptr);
@@ -222,9 +267,13 @@ cudaError_t launch_sgd(vqmc_ctx* c, const float* delta, float lr, cudaStream_t s
 // ---- adam.cu
 cudaError_t launch_mask_params(vqmc_ctx* c, cudaStream_t st);
 cudaError_t launch_refresh_weights(vqmc_ctx* c, cudaStream_t st);
-cudaError_t launch_adam(vqmc_ctx* c, const float* d_grad, cudaStream_t st);
-// advances the step count t; the factors of step t
-AdamStep adam_advance(vqmc_ctx* c);
+// advance = false: the step count and factors were already advanced
+cudaError_t launch_adam(vqmc_ctx* c, const float* d_grad, cudaStream_t st, bool advance = true);
+// advances the step count t (host mirror and, on `st`, the device state,
+// which computes the factors of step t); returns the factors' location
+AdamStep adam_advance(vqmc_ctx* c, cudaStream_t st);
+// writes the host mirrors of the counters into the device state
+cudaError_t launch_set_state(vqmc_ctx* c, cudaStream_t st);
 // Adam on the biases alone (their gradients in d_grad at theta's layout)
 cudaError_t launch_adam_bias(vqmc_ctx* c, const float* d_grad, AdamStep a, cudaStream_t st);
 cudaError_t launch_dense_split(vqmc_ctx* c, cudaStream_t st);

@@ -131,12 +131,19 @@ __global__ void eloc_dense_finish_kernel(int B, int n, int ntiles, const float* 
 }
 
 // FP64 statistics of B energies in one CTA with a fixed reduction order.
+// With ds set, thread 0 also starts the next Adam step (t += 1 and its bias
+// corrections), which the gradient kernels after it read.
 template <typename A>
 __global__ void __launch_bounds__(1024) stats_kernel(int B, const A* __restrict__ E, double* __restrict__ out,
-                                                     float* __restrict__ coef, uint32_t* __restrict__ err) {
+                                                     float* __restrict__ coef, uint32_t* __restrict__ err,
+                                                     DevState* ds, float beta1, float beta2) {
   __shared__ double s_sum[1024], s_min[1024], s_max[1024];
   __shared__ double s_mean;
   const int t = threadIdx.x;
+  if (ds && t == 0) {
+    ds->adam_t += 1;
+    adam_factors(ds, beta1, beta2);
+  }
   double sum = 0.0, mn = 1.0 / 0.0, mx = -1.0 / 0.0;
   for (int b = t; b < B; b += 1024) {
     const double x = (double)E[b];
@@ -256,12 +263,14 @@ cudaError_t launch_eloc_dense_finish(const vqmc_ctx* c, int B, const int8_t* d_s
 }
 
 cudaError_t launch_stats(const vqmc_ctx* c, int B, const void* d_e, double* d_stats, float* d_coef,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool advance) {
   if (B <= 0) return cudaSuccess;
+  DevState* ds = advance ? c->dstate : nullptr;
+  const float b1 = c->cfg.beta1, b2 = c->cfg.beta2;
   if (c->ham == VQMC_HAM_SPARSE_I32)
-    stats_kernel<int32_t><<<1, 1024, 0, st>>>(B, (const int32_t*)d_e, d_stats, d_coef, c->err);
+    stats_kernel<int32_t><<<1, 1024, 0, st>>>(B, (const int32_t*)d_e, d_stats, d_coef, c->err, ds, b1, b2);
   else
-    stats_kernel<float><<<1, 1024, 0, st>>>(B, (const float*)d_e, d_stats, d_coef, c->err);
+    stats_kernel<float><<<1, 1024, 0, st>>>(B, (const float*)d_e, d_stats, d_coef, c->err, ds, b1, b2);
   return cudaGetLastError();
 }
 

@@ -63,7 +63,8 @@ struct GemmArgs {
   int ld_cp_t;
   T* cp_row;
   int ld_cp_row, cp_shift;
-  float lr, beta1, beta2, ibc1, ibc2, eps;  // ibc = 1 / (1 - beta^t)
+  float lr, beta1, beta2, eps;
+  const float* ibc;  // device {1 / (1 - beta1^t), 1 / (1 - beta2^t)}
 };
 
 // K-range [lo, hi) of the N-tile [n0, n1) (clamped to N) for op.

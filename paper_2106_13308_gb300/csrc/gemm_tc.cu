@@ -148,6 +148,7 @@ constexpr int kStageLd = kHalf + 1;
 // is stored, zero outside the mask.
 __device__ __forceinline__ void wgrad_block(const GemmArgs<bf16>& g, bool fused, float* G, int m0w, int c0,
                                             int lane, int kl_me, int kh_me) {
+  const float ibc1 = fused ? __ldg(g.ibc) : 0.0f, ibc2 = fused ? __ldg(g.ibc + 1) : 0.0f;
   for (int r0 = 0; r0 < 32; r0 += 4) {
     float gq[8], mq[8], vq[8], tq[8];
     bool keep[8], in[8];
@@ -179,7 +180,7 @@ __device__ __forceinline__ void wgrad_block(const GemmArgs<bf16>& g, bool fused,
       if (keep[j]) {
         const float mn = g.beta1 * mq[j] + (1.0f - g.beta1) * gq[j];
         const float vn = g.beta2 * vq[j] + (1.0f - g.beta2) * gq[j] * gq[j];
-        t = tq[j] - g.lr * (mn * g.ibc1) / (sqrtf(vn * g.ibc2) + g.eps);
+        t = tq[j] - g.lr * (mn * ibc1) / (sqrtf(vn * ibc2) + g.eps);
         __stcs(g.adam_m + q, mn);
         __stcs(g.adam_v + q, vn);
         __stcs(g.theta + q, t);

@@ -43,9 +43,10 @@ cudaError_t launch_uniforms(int B, int n, uint64_t seed, uint64_t iteration, flo
 }
 
 cudaError_t launch_sampler(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,
-                           float* d_logp, cudaStream_t st) {
+                           float* d_logp, cudaStream_t st, const unsigned long long* it_dev) {
   if (B <= 0) return cudaSuccess;
-  if (c->sampler == VQMC_SAMPLER_TENSOR_CORE) return launch_sampler_tc(c, B, d_u, iteration, d_s, d_logp, st);
+  if (c->sampler == VQMC_SAMPLER_TENSOR_CORE)
+    return launch_sampler_tc(c, B, d_u, iteration, d_s, d_logp, st, nullptr, nullptr, nullptr, it_dev);
   SamplerArgs a;
   a.n = c->n;
   a.h = c->h;
@@ -60,6 +61,7 @@ cudaError_t launch_sampler(const vqmc_ctx* c, int B, const float* d_u, uint64_t 
   a.key1 = (uint32_t)(c->cfg.seed >> 32);
   a.it0 = (uint32_t)iteration;
   a.it1 = (uint32_t)(iteration >> 32);
+  a.it_dev = it_dev;
   a.s_out = d_s;
   a.logp = d_logp;
   a.err = c->err;

@@ -291,7 +291,12 @@ struct Run {
   int m0, m1;           // degrees of this lane's units in the mixed slot
   typename K::PR wp[U2], wq;  // this step's weight pairs, loaded one step ahead
 
-  __device__ __forceinline__ Run(const SamplerArgs& a) : g(a) {}
+  uint32_t it0, it1;    // Philox iteration words
+
+  __device__ __forceinline__ Run(const SamplerArgs& a) : g(a) {
+    const unsigned long long it = a.it_dev ? *a.it_dev : ((unsigned long long)a.it1 << 32 | a.it0);
+    it0 = (uint32_t)it, it1 = (uint32_t)(it >> 32);
+  }
 
   __device__ __forceinline__ void issue(int q) {
     const int s = q % nst;
@@ -355,7 +360,7 @@ struct Run {
         for (int e = 0; e < 4; ++e) uw[e] = logit(unx[e]);
         if (t + UWIN < n) load_u(t + UWIN, unx);
       } else {
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)((t + 4 * ug) >> 2), (uint32_t)ub, g.it0, g.it1), g.key0,
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)((t + 4 * ug) >> 2), (uint32_t)ub, it0, it1), g.key0,
                                       g.key1);
         uw[0] = logit(to_unit(r.x)), uw[1] = logit(to_unit(r.y));
         uw[2] = logit(to_unit(r.z)), uw[3] = logit(to_unit(r.w));

@@ -89,6 +89,7 @@ struct TcArgs {
   const float* b2;
   const float* u;     // [B][n] or null (internal Philox)
   uint32_t key0, key1, it0, it1;
+  const unsigned long long* it_dev;  // if not null: the Philox iteration, read on the device
   int8_t* s_out;      // [B][n]
   float* logp;        // [B] or null
   uint32_t* err;
@@ -298,6 +299,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* HfS = reinterpret_cast<float*>(sm + kOffHF);
   uint32_t* SB = reinterpret_cast<uint32_t*>(sm + kOffSB);
   int* CU = reinterpret_cast<int*>(sm + kOffCU);
+  const unsigned long long it_all = g.it_dev ? *g.it_dev : ((unsigned long long)g.it1 << 32 | g.it0);
+  const uint32_t it0 = (uint32_t)it_all, it1 = (uint32_t)(it_all >> 32);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + kOffBar);
   uint64_t* empty = full + kNStage;
   uint64_t* zfull = empty + kNStage;
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int w = 0; w < 4; ++w)
             dst[w * kS] = (bb < g.B && t + w < n) ? logit(__ldg(g.u + (size_t)bb * n + t + w)) : 0.0f;
         } else {
-          const uint4 r = philox4x32_10(make_uint4((uint32_t)(t >> 2), (uint32_t)bb, g.it0, g.it1), g.key0, g.key1);
+          const uint4 r = philox4x32_10(make_uint4((uint32_t)(t >> 2), (uint32_t)bb, it0, it1), g.key0, g.key1);
           dst[0] = logit(to_unit(r.x));
           dst[kS] = logit(to_unit(r.y));
           dst[2 * kS] = logit(to_unit(r.z));
@@ -715,7 +718,8 @@ int sampler_tc_block(const vqmc_ctx* c) {
 }
 
 cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,
-                              float* d_logp, cudaStream_t st, void* sx, void* stt, uint32_t* sbits) {
+                              float* d_logp, cudaStream_t st, void* sx, void* stt, uint32_t* sbits,
+                              const unsigned long long* it_dev) {
   const int D = sampler_tc_block(c);
   if (D == 0 || !gemm_tc_available()) return cudaErrorNotSupported;
   if (B <= 0) return cudaSuccess;
@@ -745,6 +749,7 @@ cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64
   a.key1 = (uint32_t)(c->cfg.seed >> 32);
   a.it0 = (uint32_t)iteration;
   a.it1 = (uint32_t)(iteration >> 32);
+  a.it_dev = it_dev;
   a.s_out = d_s;
   a.logp = d_logp;
   a.err = c->err;

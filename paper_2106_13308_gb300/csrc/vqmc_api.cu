@@ -1,6 +1,7 @@
 // C ABI of libvqmc (include/vqmc.h): context management and the VQMC
 // iteration of the paper (Sec. 2.1, 2.3, 4, 5.1) as a sequence of kernels on
 // one stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -151,7 +152,7 @@ cudaError_t launch_gemm(const vqmc_ctx* c, GemmOp op, int B, const int8_t* d_s, 
       a.cp_row = row ? (bf16*)(op == kOpDV ? c->v_s : c->wt_s) : nullptr;
       a.ld_cp_row = c->hp, a.cp_shift = op == kOpDV ? 0 : 1;
       a.lr = c->cfg.lr, a.beta1 = c->cfg.beta1, a.beta2 = c->cfg.beta2, a.eps = c->cfg.eps;
-      a.ibc1 = fuse->ibc1, a.ibc2 = fuse->ibc2;
+      a.ibc = fuse->ibc;
     }
     // BF16 GEMMs run on the tcgen05 tensor cores only (sm_103a); no fallback
     return launch_gemm_tc_bf16(a, st);
@@ -290,6 +291,7 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
   VQ_ALLOC(c->col_part, (size_t)c->col_part_tiles * c->col_part_ld * 4);
   VQ_ALLOC(c->err, 16);
   VQ_ALLOC(c->step_stats, sizeof(vqmc_step_stats));
+  VQ_ALLOC(c->dstate, sizeof(DevState));
 
   // instance
   uint64_t hsh = 1469598103934665603ull;
@@ -374,6 +376,7 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
 
 void vqmc_destroy(vqmc_ctx* c) {
   if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->events) {
     for (int64_t q = 0; q < kMaxTimedSteps * (VQMC_NUM_PARTS + 1); ++q) cudaEventDestroy(c->events[q]);
     delete[] c->events;
@@ -382,7 +385,8 @@ void vqmc_destroy(vqmc_ctx* c) {
                   c->col, c->w, c->field, c->J, c->J_hi, c->J_lo, c->S, c->E, c->Sx, c->St, c->H, c->Ht,
                   c->D, c->Dt, c->GAt, c->logp, c->coef, c->stats, c->row_part, c->col_part, c->err,
                   c->step_stats, c->Sbits, c->eloc_part, c->eloc_slice, c->erow, c->alpha, c->tim_A,
-                  c->tim_S8, c->tim_H, c->tim_row_part, c->sr_A, c->sr_x, c->sr_ones};
+                  c->tim_S8, c->tim_H, c->tim_row_part, c->sr_A, c->sr_x, c->sr_ones, c->sr_xinv,
+                  c->sr_events, c->dstate};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -408,6 +412,7 @@ vqmc_status vqmc_set_params(vqmc_ctx* c, const float* theta, int on_device, vqmc
   VQ_CUDA(cudaMemsetAsync(c->adam_m, 0, c->d * 4, S(stream)));
   VQ_CUDA(cudaMemsetAsync(c->adam_v, 0, c->d * 4, S(stream)));
   c->adam_t = 0;
+  VQ_CUDA(launch_set_state(c, S(stream)));
   vqmc_status s = vqmc_params_updated(c, stream);
   if (s != VQMC_OK) return s;
   if (!on_device) VQ_CUDA(cudaStreamSynchronize(S(stream)));
@@ -515,14 +520,17 @@ vqmc_status vqmc_adam(vqmc_ctx* c, const float* d_grad, vqmc_stream stream) {
 }  // extern "C"
 
 namespace {
-__global__ void fill_step_stats(const double* st, uint64_t it, const uint32_t* err, vqmc_step_stats* out) {
+// The step's record, and the device iteration counter advanced for the next
+// step (the sampler of this step read it).
+__global__ void fill_step_stats(const double* st, DevState* ds, const uint32_t* err, vqmc_step_stats* out) {
   out->mean = st[0];
   out->var = st[1];
   out->min = st[2];
   out->max = st[3];
-  out->iteration = it;
+  out->iteration = ds->iter;
   out->error_flags = *err;
   out->reserved = 0;
+  ds->iter += 1;
 }
 }  // namespace
 
@@ -544,8 +552,11 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
   // produce them (timed with the energy part)
   const bool tc = c->sampler == VQMC_SAMPLER_TENSOR_CORE;
   const bool sparse = c->ham != VQMC_HAM_DENSE_F32;
-  if (tc) VQ_CUDA(launch_sampler_tc(c, B, nullptr, c->iter, c->S, nullptr, st, c->Sx, c->St, sparse ? c->Sbits : nullptr));
-  else VQ_CUDA(launch_sampler(c, B, nullptr, c->iter, c->S, nullptr, st));
+  const unsigned long long* it_dev = &c->dstate->iter;
+  if (tc)
+    VQ_CUDA(launch_sampler_tc(c, B, nullptr, c->iter, c->S, nullptr, st, c->Sx, c->St, sparse ? c->Sbits : nullptr,
+                              it_dev));
+  else VQ_CUDA(launch_sampler(c, B, nullptr, c->iter, c->S, nullptr, st, it_dev));
   mark(1);
   if (!tc) VQ_CUDA(launch_spins_to_operands(c, B, c->S, c->Sx, c->St, st));
   // (c) local energies
@@ -559,31 +570,33 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
   int tim_launches = 0;
   VQ_CUDA(launch_tim_offdiag(c, B, c->S, (float*)c->E, st, &tim_launches));
   mark(2);
-  // (d) FP64 statistics and score-function coefficients
-  VQ_CUDA(launch_stats(c, B, c->E, c->stats, c->coef, st));
+  // (d) FP64 statistics and score-function coefficients; the same kernel
+  // starts this iteration's Adam step on the device (step count, factors)
+  VQ_CUDA(launch_stats(c, B, c->E, c->stats, c->coef, st, /*advance=*/true));
+  c->adam_t += 1;
   mark(3);
   // (b) + adjoint: gradient with recomputed hidden activations; for BF16 the
   // weight-gradient GEMMs apply the Adam step to the weights themselves
   const bool fuse = c->prec == VQMC_PREC_BF16;
-  AdamStep astep{};
-  if (fuse) astep = adam_advance(c);
+  const AdamStep astep{&c->dstate->ibc1};
   s = backward_from_operands(c, B, c->S, c->coef, c->grad, st, fuse ? &astep : nullptr);
   if (s != VQMC_OK) return s;
   mark(4);
   if (fuse) VQ_CUDA(launch_adam_bias(c, c->grad, astep, st));
-  else VQ_CUDA(launch_adam(c, c->grad, st));
+  else VQ_CUDA(launch_adam(c, c->grad, st, /*advance=*/false));
   // the next step's sampler streams v_s and w_s: have them in L2 (the
   // optimiser's traffic evicted them)
   if (c->sampler == VQMC_SAMPLER_TENSOR_CORE) VQ_CUDA(launch_prefetch_sampler_weights(c, st));
   mark(5);
-  fill_step_stats<<<1, 1, 0, st>>>(c->stats, c->iter, c->err, c->step_stats);
+  fill_step_stats<<<1, 1, 0, st>>>(c->stats, c->dstate, c->err, c->step_stats);
   VQ_CUDA(cudaGetLastError());
   if (h_out) VQ_CUDA(cudaMemcpyAsync(h_out, c->step_stats, sizeof(vqmc_step_stats), cudaMemcpyDeviceToHost, st));
   if (timed) {
     c->timed_steps += 1;
     // sampler (+ operand layouts unless the tensor-core sampler writes them), energy (dense: GEMM +
-    // finish; sparse: [pack,] slices [, slice sum]), stats, 7 gradient kernels, [Adam with the
-    // weight-copy refresh unless fused into the gradient GEMMs,] bias Adam, [2 L2 prefetches,] step stats
+    // finish; sparse: [pack,] slices [, slice sum]), stats (with the Adam step counter), 7 gradient
+    // kernels, [Adam with the weight-copy refresh unless fused into the gradient GEMMs,] bias Adam,
+    // [2 L2 prefetches,] step stats
     const int sampler = tc ? 1 : 2;
     const int energy = !sparse ? 2 : (tc ? 0 : 1) + 1 + (c->eloc_slices > 1 ? 1 : 0);
     c->launches += sampler + energy + tim_launches + 1 + 7 + (fuse ? 1 : 2) + (tc ? 2 : 0) + 1;
@@ -620,8 +633,8 @@ vqmc_status sr_operands(vqmc_ctx* c, int B, const int8_t* d_s, cudaStream_t st) 
 
 // delta = O^T x with (O O^T / B + lambda) x = (E - mean)/B (Sec. 2.1)
 vqmc_status sr_direction(vqmc_ctx* c, int B, const int8_t* d_s, const void* d_e, float lambda, float* d_delta,
-                         double* d_stats, cudaStream_t st) {
-  VQ_CUDA(launch_stats(c, B, d_e, d_stats, c->coef, st));
+                         double* d_stats, cudaStream_t st, bool stats_done = false) {
+  if (!stats_done) VQ_CUDA(launch_stats(c, B, d_e, d_stats, c->coef, st));
   vqmc_status s = sr_operands(c, B, d_s, st);
   if (s != VQMC_OK) return s;
   VQ_CUDA(launch_sr_gram(c, B, c->sr_A, sr_ld(c), 1.0f / (float)B, lambda, false, sr_blocks(B) * 64, st));
@@ -665,17 +678,103 @@ vqmc_status vqmc_sr_step(vqmc_ctx* c, int32_t B, float lr, float lambda, vqmc_st
   if (!(lambda > 0.0f) || !std::isfinite(lambda)) return fail(VQMC_ERR_INVALID_ARG, "lambda must be finite and > 0");
   if (!std::isfinite(lr)) return fail(VQMC_ERR_INVALID_ARG, "lr must be finite");
   cudaStream_t st = S(stream);
-  VQ_CUDA(launch_sampler(c, B, nullptr, c->iter, c->S, nullptr, st));
-  s = vqmc_local_energy(c, B, c->S, c->E, stream);
+  const bool timed = c->timing && c->timed_steps < kMaxTimedSteps;
+  cudaEvent_t* ev = timed ? c->events + c->timed_steps * (VQMC_NUM_PARTS + 1) : nullptr;
+  auto mark = [&](int part) {
+    if (ev) cudaEventRecord(ev[part], st);
+  };
+  mark(0);
+  VQ_CUDA(launch_sampler(c, B, nullptr, c->iter, c->S, nullptr, st, &c->dstate->iter));
+  mark(1);
+  if (c->ham == VQMC_HAM_DENSE_F32) {
+    VQ_CUDA(launch_spins_to_operands(c, B, c->S, c->Sx, nullptr, st));
+    VQ_CUDA(launch_gemm(c, kOpEloc, B, c->S, nullptr, nullptr, st));
+    VQ_CUDA(launch_eloc_dense_finish(c, B, c->S, c->E, st));
+  } else {
+    VQ_CUDA(launch_eloc_sparse(c, B, c->S, c->E, st));
+  }
+  int tim_launches = 0;
+  VQ_CUDA(launch_tim_offdiag(c, B, c->S, (float*)c->E, st, &tim_launches));
+  mark(2);
+  VQ_CUDA(launch_stats(c, B, c->E, c->stats, c->coef, st));
+  mark(3);
+  s = sr_direction(c, B, c->S, c->E, lambda, c->grad, c->stats, st, /*stats_done=*/true);
   if (s != VQMC_OK) return s;
-  s = sr_direction(c, B, c->S, c->E, lambda, c->grad, c->stats, st);
-  if (s != VQMC_OK) return s;
+  mark(4);
   VQ_CUDA(launch_sgd(c, c->grad, lr, st));
   VQ_CUDA(launch_refresh_weights(c, st));
-  fill_step_stats<<<1, 1, 0, st>>>(c->stats, c->iter, c->err, c->step_stats);
+  mark(5);
+  fill_step_stats<<<1, 1, 0, st>>>(c->stats, c->dstate, c->err, c->step_stats);
   VQ_CUDA(cudaGetLastError());
   if (h_out) VQ_CUDA(cudaMemcpyAsync(h_out, c->step_stats, sizeof(vqmc_step_stats), cudaMemcpyDeviceToHost, st));
+  if (timed) {
+    c->timed_steps += 1;
+    // sampler, energy (dense: operands + GEMM + finish; sparse: pack + slices [+ sum]) [+ transverse
+    // field], stats, SR direction (operands + 3 GEMMs, Gram, 2T - 1 Cholesky launches, solve, 7
+    // adjoint kernels), SGD, refresh (3), step stats
+    const int energy = c->ham == VQMC_HAM_DENSE_F32 ? 3 : 2 + (c->eloc_slices > 1 ? 1 : 0);
+    c->launches += 1 + energy + tim_launches + 1 + (4 + 1 + 2 * sr_blocks(B) + 7) + 1 + 3 + 1;
+  }
   c->iter += 1;
+  return VQMC_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------- captured iterations
+
+extern "C" {
+
+vqmc_status vqmc_graph_capture(vqmc_ctx* c, int32_t B, int32_t steps, int32_t optimizer, float sr_lr,
+                               float sr_lambda, vqmc_stream stream) {
+  vqmc_status s = check_B(c, B);
+  if (s != VQMC_OK) return s;
+  if (B == 0 || steps < 1) return fail(VQMC_ERR_INVALID_ARG, "graph capture needs B >= 1 and steps >= 1");
+  if (optimizer != VQMC_OPT_ADAM && optimizer != VQMC_OPT_SR) return fail(VQMC_ERR_INVALID_ARG, "bad optimizer");
+  if (!stream) return fail(VQMC_ERR_INVALID_ARG, "graph capture needs a stream other than the legacy default stream");
+  if (optimizer == VQMC_OPT_SR) {
+    s = sr_check(c, B);  // allocates the SR workspace outside the capture
+    if (s != VQMC_OK) return s;
+  }
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_steps = 0;
+  }
+  cudaStream_t st = S(stream);
+  const bool timing = c->timing;
+  const uint64_t iter0 = c->iter;
+  const int64_t t0 = c->adam_t;
+  c->timing = false;
+  VQ_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  for (int q = 0; q < steps && s == VQMC_OK; ++q)
+    s = optimizer == VQMC_OPT_SR ? vqmc_sr_step(c, B, sr_lr, sr_lambda, stream, nullptr) : vqmc_step(c, B, stream, nullptr);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  // capturing enqueues nothing: the counters stay where they were
+  c->timing = timing, c->iter = iter0, c->adam_t = t0;
+  if (s != VQMC_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return s != VQMC_OK ? s : fail(VQMC_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    c->graph = nullptr;
+    return fail(VQMC_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(ei));
+  }
+  c->graph_steps = steps;
+  c->graph_adam = optimizer == VQMC_OPT_ADAM;
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_graph_launch(vqmc_ctx* c, vqmc_stream stream, vqmc_step_stats* h_out) {
+  if (!c) return fail(VQMC_ERR_INVALID_ARG, "null context");
+  if (!c->graph) return fail(VQMC_ERR_INVALID_ARG, "no captured iterations (vqmc_graph_capture)");
+  VQ_CUDA(cudaGraphLaunch(c->graph, S(stream)));
+  c->iter += (uint64_t)c->graph_steps;
+  if (c->graph_adam) c->adam_t += c->graph_steps;
+  if (h_out) VQ_CUDA(cudaMemcpyAsync(h_out, c->step_stats, sizeof(vqmc_step_stats), cudaMemcpyDeviceToHost, S(stream)));
   return VQMC_OK;
 }
 
@@ -688,11 +787,19 @@ struct vqmc_batch {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> done;  // one per internal stream
   cudaEvent_t fork = nullptr;
+  // schedule: internal streams in use (0 = all) and member -> stream (empty:
+  // member i on stream i mod streams in use)
+  int used = 0;
+  std::vector<int> assign;
+  // captured batched iterations (vqmc_batch_graph_capture)
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
 };
 
 namespace {
 
 void batch_free(vqmc_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
   for (vqmc_ctx* c : b->members) vqmc_destroy(c);
   for (cudaEvent_t e : b->done) cudaEventDestroy(e);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
@@ -752,17 +859,174 @@ vqmc_status vqmc_batch_step(vqmc_batch* b, const int32_t* B, vqmc_stream stream,
   if (!b || !B) return fail(VQMC_ERR_INVALID_ARG, "null argument");
   cudaStream_t st = S(stream);
   VQ_CUDA(cudaEventRecord(b->fork, st));
-  const size_t k = b->streams.size();
+  const size_t k = b->used > 0 ? (size_t)b->used : b->streams.size();
   for (size_t q = 0; q < k; ++q) VQ_CUDA(cudaStreamWaitEvent(b->streams[q], b->fork, 0));
   vqmc_status first = VQMC_OK;
-  for (size_t i = 0; i < b->members.size() && first == VQMC_OK; ++i)
-    first = vqmc_step(b->members[i], B[i], (vqmc_stream)b->streams[i % k], h_out ? &h_out[i] : nullptr);
+  for (size_t i = 0; i < b->members.size() && first == VQMC_OK; ++i) {
+    const size_t q = b->assign.empty() ? i % k : (size_t)b->assign[i];
+    first = vqmc_step(b->members[i], B[i], (vqmc_stream)b->streams[q], h_out ? &h_out[i] : nullptr);
+  }
   // join every internal stream back into the caller's, also after a failure
   for (size_t q = 0; q < k; ++q) {
     VQ_CUDA(cudaEventRecord(b->done[q], b->streams[q]));
     VQ_CUDA(cudaStreamWaitEvent(st, b->done[q], 0));
   }
   return first;
+}
+
+vqmc_status vqmc_batch_graph_capture(vqmc_batch* b, const int32_t* B, int32_t steps, vqmc_stream stream) {
+  if (!b || !B) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  if (steps < 1) return fail(VQMC_ERR_INVALID_ARG, "steps must be >= 1");
+  if (!stream) return fail(VQMC_ERR_INVALID_ARG, "graph capture needs a stream other than the legacy default stream");
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    vqmc_status s = check_B(b->members[i], B[i]);
+    if (s != VQMC_OK) return s;
+    if (B[i] == 0) return fail(VQMC_ERR_INVALID_ARG, "every member needs B >= 1");
+  }
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_steps = 0;
+  }
+  const size_t m = b->members.size();
+  std::vector<uint64_t> it0(m);
+  std::vector<int64_t> t0(m);
+  std::vector<char> timing(m);
+  for (size_t i = 0; i < m; ++i) {
+    it0[i] = b->members[i]->iter, t0[i] = b->members[i]->adam_t, timing[i] = b->members[i]->timing;
+    b->members[i]->timing = false;
+  }
+  cudaStream_t st = S(stream);
+  VQ_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  vqmc_status s = VQMC_OK;
+  for (int q = 0; q < steps && s == VQMC_OK; ++q) s = vqmc_batch_step(b, B, stream, nullptr);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  for (size_t i = 0; i < m; ++i)
+    b->members[i]->iter = it0[i], b->members[i]->adam_t = t0[i], b->members[i]->timing = timing[i] != 0;
+  if (s != VQMC_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return s != VQMC_OK ? s : fail(VQMC_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    b->graph = nullptr;
+    return fail(VQMC_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(ei));
+  }
+  b->graph_steps = steps;
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_batch_graph_launch(vqmc_batch* b, vqmc_stream stream, vqmc_step_stats* h_out) {
+  if (!b) return fail(VQMC_ERR_INVALID_ARG, "null batch");
+  if (!b->graph) return fail(VQMC_ERR_INVALID_ARG, "no captured iterations (vqmc_batch_graph_capture)");
+  VQ_CUDA(cudaGraphLaunch(b->graph, S(stream)));
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    vqmc_ctx* c = b->members[i];
+    c->iter += (uint64_t)b->graph_steps;
+    c->adam_t += b->graph_steps;
+    if (h_out)
+      VQ_CUDA(cudaMemcpyAsync(&h_out[i], c->step_stats, sizeof(vqmc_step_stats), cudaMemcpyDeviceToHost, S(stream)));
+  }
+  return VQMC_OK;
+}
+
+namespace {
+
+// device milliseconds of `reps` launches of the batch's graph on st
+vqmc_status time_batch_graph(vqmc_batch* b, cudaStream_t st, int reps, double* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  VQ_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(VQMC_ERR_CUDA, "event creation failed");
+  }
+  vqmc_status s = VQMC_OK;
+  cudaError_t e = cudaEventRecord(e0, st);
+  for (int r = 0; r < reps && s == VQMC_OK && e == cudaSuccess; ++r) s = vqmc_batch_graph_launch(b, st, nullptr);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float f = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&f, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != VQMC_OK) return s;
+  if (e != cudaSuccess) return fail(VQMC_ERR_CUDA, std::string("timing: ") + cudaGetErrorString(e));
+  *ms = (double)f / reps;
+  return VQMC_OK;
+}
+
+}  // namespace
+
+vqmc_status vqmc_batch_autotune(vqmc_batch* b, const int32_t* B, vqmc_stream stream, int32_t* streams_out,
+                                double* ms_out) {
+  if (!b || !B) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  if (!stream) return fail(VQMC_ERR_INVALID_ARG, "autotuning captures graphs: pass a non-default stream");
+  cudaStream_t st = S(stream);
+  const size_t m = b->members.size();
+  // 1. cost of one iteration of each member alone (after one warm-up step)
+  std::vector<double> cost(m, 0.0);
+  {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    VQ_CUDA(cudaEventCreate(&e0));
+    VQ_CUDA(cudaEventCreate(&e1));
+    vqmc_status s = VQMC_OK;
+    for (size_t i = 0; i < m && s == VQMC_OK; ++i) {
+      s = vqmc_step(b->members[i], B[i], stream, nullptr);
+      if (s == VQMC_OK && cudaEventRecord(e0, st) != cudaSuccess) s = fail(VQMC_ERR_CUDA, "event record failed");
+      if (s == VQMC_OK) s = vqmc_step(b->members[i], B[i], stream, nullptr);
+      if (s == VQMC_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+        s = fail(VQMC_ERR_CUDA, "event timing failed");
+      float f = 0.0f;
+      if (s == VQMC_OK) cudaEventElapsedTime(&f, e0, e1);
+      cost[i] = f;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != VQMC_OK) return s;
+  }
+  // 2. candidate schedules: 1, 2, 4, 8 streams (up to the batch's), members
+  // round-robin in index order or longest-first onto the least-loaded stream
+  std::vector<size_t> order(m);
+  for (size_t i = 0; i < m; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+  double best = -1.0;
+  int best_used = 1;
+  std::vector<int> best_assign;
+  const int smax = (int)b->streams.size();
+  std::vector<int> counts;
+  for (int S = 1; S < smax; S *= 2) counts.push_back(S);
+  counts.push_back(smax);
+  for (int S : counts) {
+    for (int lpt = 0; lpt < (S > 1 ? 2 : 1); ++lpt) {
+      std::vector<int> assign(m);
+      if (lpt) {
+        std::vector<double> load(S, 0.0);
+        for (size_t i : order) {
+          const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+          assign[i] = q;
+          load[q] += cost[i];
+        }
+      } else {
+        for (size_t i = 0; i < m; ++i) assign[i] = (int)(i % S);
+      }
+      b->used = S, b->assign = assign;
+      vqmc_status s = vqmc_batch_graph_capture(b, B, 1, stream);
+      double ms = 0.0;
+      if (s == VQMC_OK) s = time_batch_graph(b, st, 1, &ms);  // warm-up
+      if (s == VQMC_OK) s = time_batch_graph(b, st, 3, &ms);
+      if (s != VQMC_OK) return s;
+      if (best < 0.0 || ms < best) best = ms, best_used = S, best_assign = assign;
+    }
+  }
+  // 3. keep the fastest schedule and its graph
+  b->used = best_used, b->assign = best_assign;
+  vqmc_status s = vqmc_batch_graph_capture(b, B, 1, stream);
+  if (s != VQMC_OK) return s;
+  if (streams_out) *streams_out = best_used;
+  if (ms_out) *ms_out = best;
+  return VQMC_OK;
 }
 
 vqmc_status vqmc_timing_enable(vqmc_ctx* c, int enable) {
@@ -883,6 +1147,7 @@ vqmc_status vqmc_load(vqmc_ctx* c, const char* path) {
   c->adam_t = hd.adam_t;
   c->iter = hd.iter;
   c->cfg.seed = hd.seed;
+  VQ_CUDA(launch_set_state(c, 0));
   VQ_CUDA(launch_refresh_weights(c, 0));
   VQ_CUDA(cudaDeviceSynchronize());
   return VQMC_OK;

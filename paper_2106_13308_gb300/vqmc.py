@@ -37,8 +37,10 @@ EXPORTS = [
     "vqmc_last_batch", "vqmc_iteration", "vqmc_check", "vqmc_save", "vqmc_load", "vqmc_timing_enable",
     "vqmc_timing_read", "vqmc_logprob_noalloc", "vqmc_last_error", "vqmc_batch_create", "vqmc_batch_destroy",
     "vqmc_batch_count", "vqmc_batch_member", "vqmc_batch_step", "vqmc_sr_gram", "vqmc_sr_direction",
-    "vqmc_sr_step",
+    "vqmc_sr_step", "vqmc_graph_capture", "vqmc_graph_launch", "vqmc_batch_graph_capture",
+    "vqmc_batch_graph_launch", "vqmc_batch_autotune",
 ]
+OPT = {"adam": 0, "sr": 1}
 PARTS = ["sample", "energy", "stats", "grad", "adam"]
 
 
@@ -115,6 +117,12 @@ def load_library(path: str = LIB_PATH):
         "vqmc_sr_gram": (st, [P, I32, P, P, P]),
         "vqmc_sr_direction": (st, [P, I32, P, P, ctypes.c_float, P, P, P]),
         "vqmc_sr_step": (st, [P, I32, ctypes.c_float, ctypes.c_float, P, ctypes.POINTER(StepStats)]),
+        "vqmc_graph_capture": (st, [P, I32, I32, I32, ctypes.c_float, ctypes.c_float, P]),
+        "vqmc_graph_launch": (st, [P, P, ctypes.POINTER(StepStats)]),
+        "vqmc_batch_graph_capture": (st, [P, ctypes.POINTER(I32), I32, P]),
+        "vqmc_batch_graph_launch": (st, [P, P, ctypes.POINTER(StepStats)]),
+        "vqmc_batch_autotune": (st, [P, ctypes.POINTER(I32), P, ctypes.POINTER(I32),
+                                     ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -231,6 +239,16 @@ def vqmc_sr_direction(ctx, B: int, s, e, lam: float, delta, stats=None, stream=N
 def vqmc_sr_step(ctx, B: int, lr: float, lam: float, out: StepStats | None = None, stream=None):
     _check(load_library().vqmc_sr_step(ctx, B, float(lr), float(lam), _stream(stream),
                                        ctypes.byref(out) if out is not None else None))
+
+
+def vqmc_graph_capture(ctx, B: int, steps: int, optimizer: str = "adam", sr_lr: float = 0.1,
+                       sr_lambda: float = 1e-3, stream=None):
+    _check(load_library().vqmc_graph_capture(ctx, B, steps, OPT[optimizer], float(sr_lr), float(sr_lambda),
+                                             _stream(stream)))
+
+
+def vqmc_graph_launch(ctx, out: StepStats | None = None, stream=None):
+    _check(load_library().vqmc_graph_launch(ctx, _stream(stream), ctypes.byref(out) if out is not None else None))
 
 
 def vqmc_check(ctx) -> int:
@@ -411,6 +429,14 @@ class VQMC:
         vqmc_sr_step(self.ctx, B, lr, lam, out)
         return out
 
+    # captured iterations (one CUDA graph launch each)
+    def graph_capture(self, B, steps=1, optimizer="adam", sr_lr=0.1, sr_lambda=1e-3, stream=None):
+        vqmc_graph_capture(self.ctx, B, steps, optimizer, sr_lr, sr_lambda, stream)
+
+    def graph_launch(self, out: StepStats | None = None, stream=None):
+        vqmc_graph_launch(self.ctx, out, stream)
+        return out
+
     def last_batch(self, B):
         ps, pe = ctypes.c_void_p(), ctypes.c_void_p()
         _check(load_library().vqmc_last_batch(self.ctx, ctypes.byref(ps), ctypes.byref(pe)))
@@ -498,6 +524,25 @@ class VQMCBatch:
             assert len(out) == count
             outp = out
         _check(_lib.vqmc_batch_step(self.handle, arr, _stream(stream), outp))
+
+    def _bs(self, B):
+        count = len(self.members)
+        bs = list(B) if hasattr(B, "__len__") else [int(B)] * count
+        return (ctypes.c_int32 * count)(*bs)
+
+    def graph_capture(self, B, steps=1, stream=None):
+        """Captures `steps` batched iterations as one CUDA graph."""
+        _check(_lib.vqmc_batch_graph_capture(self.handle, self._bs(B), steps, _stream(stream)))
+
+    def graph_launch(self, out=None, stream=None):
+        _check(_lib.vqmc_batch_graph_launch(self.handle, _stream(stream), out))
+
+    def autotune(self, B, stream=None):
+        """Chooses the schedule (streams, member assignment) by timing graph
+        replays; returns (streams, ms per batched iteration)."""
+        s, ms = ctypes.c_int32(), ctypes.c_double()
+        _check(_lib.vqmc_batch_autotune(self.handle, self._bs(B), _stream(stream), ctypes.byref(s), ctypes.byref(ms)))
+        return int(s.value), float(ms.value)
 
     def close(self):
         if getattr(self, "handle", None):
