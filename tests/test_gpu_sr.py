@@ -111,6 +111,36 @@ def test_sr_direction_matches_oracle(n, h, B, act, lam, kind):
     assert m.check() == 0
 
 
+def test_sr_direction_at_the_maximum_batch():
+    """B = 16384, the largest SR batch: a 256 x 256-block Cholesky (more
+    panel blocks than SMs) and a 256-block solve.  A small model keeps the
+    oracle's d x d solve cheap; with B > d the smallest eigenvalue of
+    O O^T / B + lambda is lambda, so kappa = (largest eigenvalue of
+    O^T O / B + lambda) / lambda.  One sample more is rejected."""
+    from paper_2106_13308_gb300.vqmc import VQMCError, VQMC_ERR_UNSUPPORTED
+    n, h, B, lam = 12, 6, 16384, 1e-2
+    inst = er_instance(n, 0.4, 31)
+    theta = inputs.lively_params(n, h, 32)
+    m = make_model(n, h, B, inst, act="relu", precision="fp32", theta=theta)
+    S = inputs.spins(B, n, 33)
+    Sd = torch.from_numpy(S).cuda()
+    delta, _ = m.sr_direction(Sd, m.local_energy(Sd), lam)
+    P = oracle_params(theta, n, h, "fp32")
+    code = act_code("relu")
+    dref, _ = oracle.sr_direction(P, inst, S, lam, code)
+    O = oracle.per_sample_grads(P, S, code)
+    kappa = np.linalg.eigvalsh(O.T @ O / B + lam * np.eye(O.shape[1]))[-1] / lam
+    tol = 1e-5 + 64 * kappa * U32
+    err = rel_err(delta.cpu().numpy(), dref)
+    assert err <= tol, f"rel err {err:.3g} > {tol:.3g} (kappa {kappa:.3g})"
+    assert m.check() == 0
+    del m
+    big = make_model(n, h, B + 1, inst, act="relu", precision="fp32", theta=theta)
+    with pytest.raises(VQMCError) as ei:
+        big.sr_gram(torch.from_numpy(inputs.spins(B + 1, n, 34)).cuda())
+    assert ei.value.status == VQMC_ERR_UNSUPPORTED
+
+
 def test_sr_direction_tends_to_the_gradient_for_large_lambda():
     """(I + lambda) delta = g: lambda delta -> g, the vqmc_grad result."""
     n, h, B = 40, 30, 256
