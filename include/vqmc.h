@@ -61,7 +61,7 @@ typedef enum {
   VQMC_ERR_OOM = 3,         /* device allocation failed */
   VQMC_ERR_NONFINITE = 4,   /* a NaN/Inf energy or statistic was produced */
   VQMC_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
-  VQMC_ERR_UNSUPPORTED = 6  /* size or option this build does not handle */
+  VQMC_ERR_UNSUPPORTED = 6  /* size or option the library does not handle */
 } vqmc_status;
 
 enum { VQMC_ACT_RELU = 0, VQMC_ACT_SIGMOID = 1 };
@@ -156,7 +156,7 @@ typedef struct {
  * (zero), Adam state, BF16/FP32 weight copies and every workspace for up to
  * cfg->max_batch samples, and copies the instance to the device.  Synchronous.
  * Errors: INVALID_ARG (n, h, max_batch < 1, inst->n != cfg->n, bad kind or
- * NULL arrays), OOM, CUDA, UNSUPPORTED (sizes this build cannot tile). */
+ * NULL arrays), OOM, CUDA, UNSUPPORTED (sizes the library cannot tile). */
 vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_ctx** out);
 
 /* Frees everything the context owns.  NULL is accepted. */

@@ -226,7 +226,7 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
       if (!(inst->alpha[i] >= 0.0f) || !std::isfinite(inst->alpha[i]))
         return fail(VQMC_ERR_INVALID_ARG, "alpha must be finite and >= 0");
   }
-  if (pad_up(h) > 2048) return fail(VQMC_ERR_UNSUPPORTED, "this build samples with h <= 2048");
+  if (pad_up(h) > 2048) return fail(VQMC_ERR_UNSUPPORTED, "the samplers support h <= 2048");
   if (cfg->sampler > VQMC_SAMPLER_TENSOR_CORE) return fail(VQMC_ERR_INVALID_ARG, "bad sampler");
 
   vqmc_ctx* c = new vqmc_ctx();

@@ -188,13 +188,15 @@ def test_invalid_batch_rejected():
         m.step(0)
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp32"])
-def test_full_size_er10000_sampled_outputs(prec):
+@pytest.mark.parametrize("name,prec", [("maxcut_er10000", "bf16"), ("maxcut_er10000", "fp32"),
+                                       ("maxcut_3reg1000", "bf16"), ("maxcut_3reg1000", "fp32")])
+def test_full_size_er10000_sampled_outputs(name, prec):
     """The benchmark workload (G(10000, 8/9999), weights in {1..10}, h = 2000,
-    B = 2048) in the benchmark's launch configuration, checked on outputs the
-    oracle computes one by one: every energy (bit-exact), 6 samples
-    teacher-forced, their log pi, and the gradient of 4 samples."""
-    cfg = inputs.config("maxcut_er10000")
+    B = 2048) and the random 3-regular workload (n = 1000, weights +-1,
+    h = 1000, B = 4096) at full size, checked on outputs the oracle computes
+    one by one: every energy (bit-exact), 6 samples teacher-forced, their
+    log pi, and the gradient of 4 samples."""
+    cfg = inputs.config(name)
     inst = inputs.make_instance(cfg)
     n, h, B = cfg["n"], cfg["h"], cfg["B"]
     theta = inputs.lively_params(n, h, cfg["param_seed"])
@@ -205,7 +207,7 @@ def test_full_size_er10000_sampled_outputs(prec):
     E = m.local_energy(S).cpu().numpy()
     Sn = S.cpu().numpy()
     assert np.array_equal(E.astype(np.float64), oracle.energy(inst, Sn))
-    pick = np.array([0, 1, 777, 1024, 2046, 2047])
+    pick = np.array([0, 1, 777, 1024, B - 2, B - 1])
     U = oracle.uniforms(B, n, seed, 0)[pick]
     code = act_code("relu", prec)
     mism, ties = teacher_forced(P, Sn[pick], U, code, 1e-6 if prec == "fp32" else 1e-4)
@@ -220,6 +222,38 @@ def test_full_size_er10000_sampled_outputs(prec):
     g = m.logprob_backward(S, torch.from_numpy(gout).cuda()).cpu().numpy()
     go = oracle.made_to_theta(*oracle.logprob_grad(P, Sn[gsel], gout[gsel].astype(np.float64), code))
     assert rel_err(g, go) <= (1e-4 if prec == "fp32" else 3e-2)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_full_size_sk2000_sampled_outputs(prec):
+    """The dense spin-glass workload (SK couplings J ~ N(0, 1/n), n = 2000,
+    h = 2000, B = 8192) on B seeded configurations: energies of 16 picked
+    rows against the oracle within the bound of the arithmetic (FP32:
+    n^2 2^-23 max|J|; BF16 hi/lo split of J: n^2 2^-16 max|J|), the FP64
+    statistics of all B energies against NumPy's of the same float32
+    energies, and the log pi of picked rows."""
+    cfg = inputs.config("sk2000")
+    inst = inputs.make_instance(cfg)
+    n, h, B = cfg["n"], cfg["h"], cfg["B"]
+    theta = inputs.lively_params(n, h, cfg["param_seed"])
+    m = make_model(n, h, B, inst, precision=prec, theta=theta, seed=77)
+    Sn = inputs.spins(B, n, 78)
+    S = torch.from_numpy(Sn).cuda()
+    E = m.local_energy(S)
+    st, _ = m.energy_stats(E)
+    En = E.cpu().numpy().astype(np.float64)
+    pick = np.array([0, 1, 2, 1000, 2047, 2048, 4095, 4096, 5000, 6000, 7000, 8000, 8100, 8189, 8190, 8191])
+    Eo = oracle.energy(inst, Sn[pick])
+    jmax = float(np.abs(inst["J"]).max())
+    bound = n * n * (2.0 ** -23 if prec == "fp32" else 2.0 ** -16) * jmax
+    assert np.max(np.abs(En[pick] - Eo)) <= bound
+    ref = np.array([En.mean(), En.var(), En.min(), En.max()])
+    assert np.allclose(st.cpu().numpy(), ref, rtol=1e-12)
+    P = oracle_params(theta, n, h, prec)
+    lpo = oracle.logprob(P, Sn[pick[:4]], act_code("relu", prec))
+    lpg = m.logprob(S).cpu().numpy()[pick[:4]]
+    assert logp_rel(lpg, lpo) <= (1e-5 if prec == "fp32" else 2e-2)
+    assert m.check() == 0
 
 
 @pytest.mark.slow
