@@ -387,8 +387,12 @@ vqmc_status vqmc_load(vqmc_ctx* ctx, const char* path);
  * Enabling resets the record. */
 enum {
   VQMC_PART_SAMPLE = 0,   /* the sampler kernel (uniforms generated in-kernel) */
-  VQMC_PART_ENERGY = 1,   /* local energies (and, after the CUDA-core sampler, the spins' GEMM layouts) */
-  VQMC_PART_STATS = 2,    /* FP64 statistics and coefficients */
+  VQMC_PART_ENERGY = 1,   /* local energies (and, after the CUDA-core sampler, the spins' GEMM layouts);
+                             for a sparse instance without a transverse field the energies and the
+                             statistics run beside the hidden-activation GEMM, and this part is that
+                             GEMM's time */
+  VQMC_PART_STATS = 2,    /* FP64 statistics and coefficients (in the overlapped case: the wait for
+                             them after the hidden-activation GEMM) */
   VQMC_PART_GRAD = 3,     /* log-prob forward + adjoint GEMMs and reductions; for BF16 also the
                              Adam step on the weights, which the weight-gradient GEMMs apply */
   VQMC_PART_ADAM = 4,     /* Adam step (BF16: biases only) and weight-copy refresh */

@@ -107,6 +107,10 @@ struct vqmc_ctx {
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
   bool graph_adam = false;
+  // side stream of vqmc_step: the sparse energy and the statistics run on it
+  // beside the hidden-activation GEMM (fork/join events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   // Kernel-side weight copies, element type float (FP32) or bf16 (BF16):
   //   wt_s [sampler_rows(n)][hp]  row j = column j of W1 (input j, 1-based),
@@ -210,8 +214,9 @@ cudaError_t launch_eloc_dense_finish(const vqmc_ctx* c, int B, const int8_t* d_s
 // (float [B]); *launches (if not null) receives the number of kernels
 cudaError_t launch_tim_offdiag(const vqmc_ctx* c, int B, const int8_t* d_s, float* d_e, cudaStream_t st,
                                int* launches = nullptr);
-// rows per chunk of the flipped states for at most Bmax samples
-int tim_chunk_rows(int Bmax, int n);
+// rows per chunk of the flipped states for at most Bmax samples (padded
+// sizes hp, np and the activation element size bound its workspace)
+int tim_chunk_rows(int Bmax, int n, int hp, int np, int esize);
 // advance: also start the next Adam step on the device (t += 1 and its
 // factors), saving vqmc_step a launch; the caller advances the host mirror
 cudaError_t launch_stats(const vqmc_ctx* c, int B, const void* d_e, double* d_stats, float* d_coef,

@@ -21,7 +21,11 @@
 namespace vqmc {
 namespace {
 
-constexpr int kMaxChunkRows = 32768;  // multiple of 128
+// Rows per chunk: as many as fit in about 256 MB of row workspace (the
+// hidden activations and spins of a row), between 32,768 and 131,072, a
+// multiple of 128; fewer chunks mean fewer dependent launches.
+constexpr long long kChunkBytes = 256ll << 20;
+constexpr int kMinChunkRows = 32768, kMaxChunkRows = 131072;
 
 template <typename T>
 __device__ __forceinline__ T to_t(float x);
@@ -198,10 +202,12 @@ cudaError_t offdiag(const vqmc_ctx* c, int B, const int8_t* d_s, float* d_e, cud
 
 }  // namespace
 
-int tim_chunk_rows(int Bmax, int n) {
+int tim_chunk_rows(int Bmax, int n, int hp, int np, int esize) {
   const long long total = (long long)Bmax * (n + 1);
   const long long r = (total + 127) / 128 * 128;
-  return (int)(r < kMaxChunkRows ? r : kMaxChunkRows);
+  long long cap = kChunkBytes / ((long long)hp * esize + np) / 128 * 128;
+  cap = cap < kMinChunkRows ? kMinChunkRows : (cap > kMaxChunkRows ? kMaxChunkRows : cap);
+  return (int)(r < cap ? r : cap);
 }
 
 cudaError_t launch_tim_offdiag(const vqmc_ctx* c, int B, const int8_t* d_s, float* d_e, cudaStream_t st,

@@ -172,11 +172,12 @@ namespace {
 // With fuse set (BF16), the two weight-gradient GEMMs apply that Adam step
 // to W2 and W1^T in their epilogues instead of writing dW2 and dW1^T; both
 // run after every GEMM that reads the old weights (hidden adjoint: W2).
+// With hidden_done, H and Ht already hold this batch's hidden activations.
 vqmc_status backward_from_operands(vqmc_ctx* c, int B, const int8_t* d_s, const float* gout, float* grad,
-                                   cudaStream_t st, const AdamStep* fuse = nullptr) {
+                                   cudaStream_t st, const AdamStep* fuse = nullptr, bool hidden_done = false) {
   const int n = c->n, h = c->h;
   const int mtiles = (B + 127) / 128;
-  VQ_CUDA(launch_gemm(c, kOpHidden, B, d_s, nullptr, nullptr, st));
+  if (!hidden_done) VQ_CUDA(launch_gemm(c, kOpHidden, B, d_s, nullptr, nullptr, st));
   VQ_CUDA(launch_gemm(c, kOpOut, B, d_s, gout, nullptr, st));
   VQ_CUDA(launch_col_sum(c, n, mtiles, grad + (size_t)2 * n * h + h, st));  // db2
   VQ_CUDA(launch_gemm(c, kOpGA, B, d_s, nullptr, nullptr, st));
@@ -292,6 +293,14 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
   VQ_ALLOC(c->err, 16);
   VQ_ALLOC(c->step_stats, sizeof(vqmc_step_stats));
   VQ_ALLOC(c->dstate, sizeof(DevState));
+  // the side stream's short kernels (energy, statistics) are on the critical
+  // path: give them the highest priority, the hidden GEMM fills in around them
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup_fail(VQMC_ERR_CUDA, "could not create the context's side stream");
 
   // instance
   uint64_t hsh = 1469598103934665603ull;
@@ -358,7 +367,7 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
     if (cudaMemcpy(c->alpha, inst->alpha, (size_t)n * 4, cudaMemcpyHostToDevice) != cudaSuccess)
       return cleanup_fail(VQMC_ERR_CUDA, "copy of alpha failed");
     hsh = fnv1a(hsh, inst->alpha, (size_t)n * 4);
-    c->tim_rows = tim_chunk_rows(Bmax, n);
+    c->tim_rows = tim_chunk_rows(Bmax, n, c->hp, c->np, (int)esize(c));
     const size_t rows = (size_t)c->tim_rows;
     VQ_ALLOC(c->tim_A, (size_t)Bmax * c->hp * 4);
     VQ_ALLOC(c->tim_S8, rows * c->np);
@@ -377,6 +386,9 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
 void vqmc_destroy(vqmc_ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->events) {
     for (int64_t q = 0; q < kMaxTimedSteps * (VQMC_NUM_PARTS + 1); ++q) cudaEventDestroy(c->events[q]);
     delete[] c->events;
@@ -559,27 +571,42 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
   else VQ_CUDA(launch_sampler(c, B, nullptr, c->iter, c->S, nullptr, st, it_dev));
   mark(1);
   if (!tc) VQ_CUDA(launch_spins_to_operands(c, B, c->S, c->Sx, c->St, st));
-  // (c) local energies
-  if (c->ham == VQMC_HAM_DENSE_F32) {
-    VQ_CUDA(launch_gemm(c, kOpEloc, B, c->S, nullptr, nullptr, st));
-    VQ_CUDA(launch_eloc_dense_finish(c, B, c->S, c->E, st));
-  } else {
-    VQ_CUDA(launch_eloc_sparse(c, B, c->S, c->E, st, /*packed=*/tc));
-  }
-  // transverse field: the off-diagonal part (n + 1 log-prob rows per sample)
+  // (c) local energies and (d) FP64 statistics with the score-function
+  // coefficients; the statistics kernel also starts this iteration's Adam
+  // step on the device (step count, factors).  For a sparse instance without
+  // a transverse field both need only the samples, like the hidden-activation
+  // GEMM of (b), and share no buffer with it: they run on the side stream
+  // beside that GEMM.
+  const bool overlap = sparse && !c->alpha;
   int tim_launches = 0;
-  VQ_CUDA(launch_tim_offdiag(c, B, c->S, (float*)c->E, st, &tim_launches));
-  mark(2);
-  // (d) FP64 statistics and score-function coefficients; the same kernel
-  // starts this iteration's Adam step on the device (step count, factors)
-  VQ_CUDA(launch_stats(c, B, c->E, c->stats, c->coef, st, /*advance=*/true));
+  if (overlap) {
+    VQ_CUDA(cudaEventRecord(c->ev_fork, st));
+    VQ_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    VQ_CUDA(launch_eloc_sparse(c, B, c->S, c->E, c->side, /*packed=*/tc));
+    VQ_CUDA(launch_stats(c, B, c->E, c->stats, c->coef, c->side, /*advance=*/true));
+    VQ_CUDA(cudaEventRecord(c->ev_join, c->side));
+    VQ_CUDA(launch_gemm(c, kOpHidden, B, c->S, nullptr, nullptr, st));
+    mark(2);
+    VQ_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
+  } else {
+    if (c->ham == VQMC_HAM_DENSE_F32) {
+      VQ_CUDA(launch_gemm(c, kOpEloc, B, c->S, nullptr, nullptr, st));
+      VQ_CUDA(launch_eloc_dense_finish(c, B, c->S, c->E, st));
+    } else {
+      VQ_CUDA(launch_eloc_sparse(c, B, c->S, c->E, st, /*packed=*/tc));
+    }
+    // transverse field: the off-diagonal part (n + 1 log-prob rows per sample)
+    VQ_CUDA(launch_tim_offdiag(c, B, c->S, (float*)c->E, st, &tim_launches));
+    mark(2);
+    VQ_CUDA(launch_stats(c, B, c->E, c->stats, c->coef, st, /*advance=*/true));
+  }
   c->adam_t += 1;
   mark(3);
   // (b) + adjoint: gradient with recomputed hidden activations; for BF16 the
   // weight-gradient GEMMs apply the Adam step to the weights themselves
   const bool fuse = c->prec == VQMC_PREC_BF16;
   const AdamStep astep{&c->dstate->ibc1};
-  s = backward_from_operands(c, B, c->S, c->coef, c->grad, st, fuse ? &astep : nullptr);
+  s = backward_from_operands(c, B, c->S, c->coef, c->grad, st, fuse ? &astep : nullptr, /*hidden_done=*/overlap);
   if (s != VQMC_OK) return s;
   mark(4);
   if (fuse) VQ_CUDA(launch_adam_bias(c, c->grad, astep, st));
