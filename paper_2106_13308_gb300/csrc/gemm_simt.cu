@@ -84,6 +84,15 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const GemmArgs<T> g) {
       return;
     }
   }
+  if (op == kOpOut && g.flip_rows) {
+    // single-flip rows of the transverse field: a tile whose columns all
+    // precede the flipped spin of each of its rows (one sample, no unflipped
+    // row) contributes nothing the log-ratios read, so it is skipped
+    const long long ga = g.row0 + m0;
+    const int ia = (int)(ga % (g.n + 1));
+    const int last = m1 - 1 - m0;
+    if (ia + last < g.n && n0 + BN <= ia) return;
+  }
   int klo, khi;
   gemm_k_range(op, n0, n1, g.K, g.n, g.h, &klo, &khi);
   klo = klo / BK * BK;

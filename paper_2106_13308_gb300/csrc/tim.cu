@@ -171,7 +171,7 @@ cudaError_t chunk_gemm<bf16>(const vqmc_ctx* c, GemmOp op, int rows, long long g
 }
 template <>
 cudaError_t chunk_gemm<float>(const vqmc_ctx* c, GemmOp op, int rows, long long g0, cudaStream_t st) {
-  GemmArgs<float> a = chunk_args<float>(c, op, rows);  // computes every tile
+  GemmArgs<float> a = chunk_args<float>(c, op, rows);
   a.row_part = c->tim_row_part + g0, a.row0 = g0;
   return launch_gemm_simt_f32(a, st);
 }
