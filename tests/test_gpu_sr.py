@@ -176,6 +176,25 @@ def test_sr_edge_cases_and_errors():
     assert ei.value.status == VQMC_ERR_UNSUPPORTED
 
 
+def test_sr_failed_factorisation_sets_the_error_word():
+    """A Cholesky pivot that is not positive is reported, not hidden: with
+    B = 128 samples and d = 22 parameters the Gram matrix has rank <= 22, and
+    lambda = 1e-30 leaves the remaining 106 pivots to FP32 rounding noise of
+    either sign.  The call completes (no fault, no wait), the direction is
+    not finite and vqmc_check reports VQMC_DEVERR_NONFINITE."""
+    from paper_2106_13308_gb300.vqmc import DEVERR_NONFINITE
+    n, h, B = 4, 2, 128
+    inst = er_instance(n, 0.9, 3)
+    m = make_model(n, h, B, inst, precision="fp32", theta=inputs.lively_params(n, h, 2))
+    assert m.d == 22
+    S = torch.from_numpy(inputs.spins(B, n, 5)).cuda()
+    delta, _ = m.sr_direction(S, m.local_energy(S), 1e-30)
+    torch.cuda.synchronize()
+    assert not torch.isfinite(delta).all()
+    assert m.check() & DEVERR_NONFINITE
+    assert m.check() == 0  # the word was read and cleared
+
+
 def test_sr_step_is_sgd_on_the_sr_direction():
     """One vqmc_sr_step: the oracle draws the same samples from its own
     Philox uniforms (no near-ties for these seeds) and its direction gives
