@@ -49,8 +49,16 @@ template <>
 __device__ __forceinline__ bf16 of_f<bf16>(float x) { return __float2bfloat16_rn(x); }
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
-__device__ __forceinline__ float log_sigmoidf_(float x) {
-  return x >= 0.0f ? -log1pf(expf(-x)) : x - log1pf(expf(x));
+// log sigma(x) and sigma(-x) of an output element from one exponential,
+// e = exp(-|x|): log sigma(x) = min(x, 0) - log(1 + e), sigma(-x) =
+// (x >= 0 ? e : 1) / (1 + e), on the hardware exp2/log2 approximations and
+// the approximate division (absolute error of the log term below 4e-7 for
+// 1 + e in (1, 2], relative error of sigma a few 2^-23: far inside the FP32
+// model's tolerances on log pi and the gradient)
+__device__ __forceinline__ void log_sigmoid_pair(float x, float& ls, float& sm) {
+  const float e = __expf(-fabsf(x));
+  ls = fminf(x, 0.0f) - __logf(1.0f + e);
+  sm = __fdividef(x >= 0.0f ? e : 1.0f, 1.0f + e);
 }
 
 // 8 consecutive K-elements of row r starting at k (zeros outside [.., khi) or r >= R)
@@ -177,9 +185,11 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const GemmArgs<T> g) {
         if (m < g.M && nn < g.N) {
           const float z = acc[i][j] + g.bias[nn];
           const float s = g.S8[(size_t)m * g.lds8 + nn] > 0 ? 1.0f : -1.0f;
-          rowsum[i] += log_sigmoidf_(s * z);
+          float ls, sm;
+          log_sigmoid_pair(s * z, ls, sm);
+          rowsum[i] += ls;
           if (g.coef) {
-            const float d = cm * s * sigmoidf_(-s * z);
+            const float d = cm * s * sm;
             const T tv = of_f<T>(d);
             g.out[(size_t)m * g.ldo + nn] = tv;
             g.out_t[(size_t)nn * g.ldt + m] = tv;

@@ -197,15 +197,15 @@ __global__ void __launch_bounds__(256) chol_panel_kernel(float* __restrict__ A, 
   for (int j = 0; j < kNB; ++j) {
     const float* cb = colbuf[j & 1];
     const float d = cb[j];
-    const float sd = sqrtf(d);
+    const float rs = rsqrtf(d);  // NaN for d < 0, inf for d = 0
     bad |= !(d > 0.0f);
     const float cr = cb[r];
     if (q == (j & 3)) {
-      if (r == j) v[j >> 2] = sd;
-      else if (r > j) v[j >> 2] = cr / sd;
+      if (r == j) v[j >> 2] = d * rs;
+      else if (r > j) v[j >> 2] = cr * rs;
     }
     // trailing columns c in (j, r]: A_rc -= A_rj A_cj / A_jj
-    const float ar = cr / d;
+    const float ar = cr * (rs * rs);
 #pragma unroll
     for (int m = (j + 1) >> 2; m < 16; ++m) {
       const int c = 4 * m + q;
