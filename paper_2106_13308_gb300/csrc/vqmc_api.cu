@@ -772,8 +772,8 @@ vqmc_status vqmc_graph_capture(vqmc_ctx* c, int32_t B, int32_t steps, int32_t op
   const bool timing = c->timing;
   const uint64_t iter0 = c->iter;
   const int64_t t0 = c->adam_t;
-  c->timing = false;
   VQ_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  c->timing = false;  // no timing events inside the graph
   for (int q = 0; q < steps && s == VQMC_OK; ++q)
     s = optimizer == VQMC_OPT_SR ? vqmc_sr_step(c, B, sr_lr, sr_lambda, stream, nullptr) : vqmc_step(c, B, stream, nullptr);
   cudaGraph_t g = nullptr;
@@ -919,12 +919,11 @@ vqmc_status vqmc_batch_graph_capture(vqmc_batch* b, const int32_t* B, int32_t st
   std::vector<uint64_t> it0(m);
   std::vector<int64_t> t0(m);
   std::vector<char> timing(m);
-  for (size_t i = 0; i < m; ++i) {
+  for (size_t i = 0; i < m; ++i)
     it0[i] = b->members[i]->iter, t0[i] = b->members[i]->adam_t, timing[i] = b->members[i]->timing;
-    b->members[i]->timing = false;
-  }
   cudaStream_t st = S(stream);
   VQ_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  for (size_t i = 0; i < m; ++i) b->members[i]->timing = false;  // no timing events inside the graph
   vqmc_status s = VQMC_OK;
   for (int q = 0; q < steps && s == VQMC_OK; ++q) s = vqmc_batch_step(b, B, stream, nullptr);
   cudaGraph_t g = nullptr;
