@@ -22,8 +22,9 @@
 //   P_i = 1 + sum_{k: m(k) < i} H_k H_k^T,   Q_t = 1 + sum_{j <= t} s_j s_j^T,
 // the ones standing for the two bias blocks.  Walking the spins in order and
 // the hidden units in degree order (sorted degrees) updates P and Q by one
-// outer product per event, so an entry of G costs about 3 (n + h) flops
-// instead of the 2 h n of a GEMM over explicit score vectors.
+// outer product per event, so an entry of G costs 5 (n + h) flops (three
+// FP32 instructions per event) instead of the 2 h n of a GEMM over explicit
+// score vectors.
 #include <climits>
 #include <cmath>
 #include <vector>
@@ -175,8 +176,9 @@ __global__ void __launch_bounds__(256) sr_gram_kernel(GramArgs a) {
 // the identity) for the triangular solves, which need nothing else of the
 // diagonal blocks; A_kk itself is left as it is, so that no CTA of this
 // launch can read a partly overwritten block.  CTA i > 0 solves the panel
-// block X L_kk^T = A_(k+i),k in place.  Only the lower triangle of A is read.  A non-positive pivot (rounding or non-finite input) sets the
-// device error word (VQMC_DEVERR_NONFINITE) and propagates a NaN.
+// block X L_kk^T = A_(k+i),k in place.  Only the lower triangle of A is
+// read.  A non-positive pivot (rounding or non-finite input) sets the device
+// error word (VQMC_DEVERR_NONFINITE) and propagates a NaN.
 __global__ void __launch_bounds__(256) chol_panel_kernel(float* __restrict__ A, int ld, int k, float* __restrict__ Xinv,
                                                          uint32_t* err) {
   __shared__ float L[kNB][kNB + 1];
