@@ -337,6 +337,72 @@ def _batched_arm(K, W, dist_on, world):
     return out
 
 
+def _quantisation_arm(cfg, inst):
+    """How far the BF16 path's results lie from the plain FP32 path's at the
+    benchmark workload, on the same parameters (spread-out conditionals,
+    as a trained model has) and the same uniforms: the rows that the two
+    samplers draw differently, log pi of the FP32 path's samples, and the
+    score-function gradient of those samples with their energies.  The FP32
+    path matches the exact FP64 model within 1e-5 (log pi) and 1e-4
+    (gradient) in the parity tests, so these figures state the BF16
+    quantisation error to that accuracy."""
+    import numpy as np
+    import torch
+    from paper_2106_13308_gb300 import inputs
+    from paper_2106_13308_gb300.vqmc import VQMC
+    n, h, B = cfg["n"], cfg["h"], cfg["B"]
+    theta = torch.from_numpy(inputs.lively_params(n, h, cfg["param_seed"]))
+    res = {}
+    ms = {}
+    for prec in ("bf16", "fp32"):
+        m = VQMC(n, h, B, inst, act=cfg["act"], precision=prec, seed=12345)
+        m.set_params(theta)
+        ms[prec] = m
+    Sb, _ = ms["bf16"].sample(B, None, iteration=0)
+    Sf, _ = ms["fp32"].sample(B, None, iteration=0)
+    res["rows_differing"] = float((Sb != Sf).any(dim=1).float().mean().item())
+    lpb = ms["bf16"].logprob(Sf).double()
+    lpf = ms["fp32"].logprob(Sf).double()
+    rel = ((lpb - lpf).abs() / lpf.abs()).cpu().numpy()
+    res["logp_rel_max"] = float(rel.max())
+    res["logp_rel_median"] = float(np.median(rel))
+    E = ms["fp32"].local_energy(Sf)
+    gb, _ = ms["bf16"].grad(Sf, E)
+    gf, _ = ms["fp32"].grad(Sf, E)
+    gb, gf = gb.double().cpu().numpy(), gf.double().cpu().numpy()
+    res["grad_rel"] = float(np.linalg.norm(gb - gf) / np.linalg.norm(gf))
+    nh = n * h
+    blocks = {"W1": slice(0, nh), "b1": slice(nh, nh + h), "W2": slice(nh + h, 2 * nh + h), "b2": slice(2 * nh + h, None)}
+    res["grad_rel_blocks"] = {k: float(np.linalg.norm(gb[b] - gf[b]) / max(np.linalg.norm(gf[b]), 1e-300))
+                              for k, b in blocks.items()}
+    res["params"] = "inputs.lively_params (conditionals spread over (0, 1)); Philox iteration 0, one batch"
+    for m in ms.values():
+        m.close()
+    return res
+
+
+def _equal_energy_arm(cfg, inst, seeds=5, iters=300):
+    """BF16+FP32 against plain FP32 at equal final energy: per seed, the same
+    initial parameters and Philox key at both precisions, `iters` Adam
+    iterations, then the mean energy of 1024 fresh samples; averaged over
+    the seeds (train.compare_precisions)."""
+    import torch
+    from paper_2106_13308_gb300 import inputs, train
+    from paper_2106_13308_gb300.vqmc import VQMC
+    n, h, B = cfg["n"], cfg["h"], cfg["B"]
+
+    def make(prec, seed):
+        m = VQMC(n, h, B, inst, act=cfg["act"], precision=prec, seed=100 + seed)
+        m.set_params(torch.from_numpy(inputs.made_params(n, h, cfg["param_seed"] + seed, w_std=cfg["w_std"])))
+        return m
+
+    t0 = time.perf_counter()
+    r = train.compare_precisions(make, B, seeds=seeds, iters=iters, eval_batch=1024)
+    r["wall_s"] = time.perf_counter() - t0
+    r["within_0.1pct"] = bool(r["rel_diff"] <= 1e-3)
+    return r
+
+
 def _e2e(m, B, K, W):
     """Same metric through the public Python API as a user runs it: every step
     reads the statistics and the batch's energies back to pinned host memory."""
@@ -420,6 +486,9 @@ def main():
     ap.add_argument("--sr-only", action="store_true", help="run only the stochastic reconfiguration arm")
     ap.add_argument("--no-batched", action="store_true", help="skip the many-instances arm")
     ap.add_argument("--batched-only", action="store_true", help="run only the many-instances arm")
+    ap.add_argument("--no-quant", action="store_true", help="skip the BF16-vs-FP32 quantisation figures")
+    ap.add_argument("--no-equal-energy", action="store_true",
+                    help="skip the 5-seed x 300-iteration equal-energy comparison")
     args = ap.parse_args()
     rank, world, local = _dist_env()
     W = max(args.warmup, 3)
@@ -519,6 +588,16 @@ def main():
                 "part_ms": {k: v / max(steps32, 1) for k, v in parts32.items()}}
         del m32
 
+    quant = None
+    if not args.no_quant:
+        torch.cuda.empty_cache()
+        quant = _quantisation_arm(cfg, inst)
+
+    equal = None
+    if not args.no_equal_energy and rank == 0 and world == 1:
+        torch.cuda.empty_cache()
+        equal = _equal_energy_arm(cfg, inst)
+
     tim = None
     if not args.no_tim:
         torch.cuda.empty_cache()
@@ -568,7 +647,8 @@ def main():
                 "samples_per_s": value * B,
                 # exact samples per second of the sampler alone (uniforms are drawn inside it)
                 "sampler_samples_per_s": world * B / (sample_ms / 1000.0),
-                "part_ms": part_ms, "fp32": fp32, "tim": tim, "sr": sr, "batched": batched,
+                "part_ms": part_ms, "fp32": fp32, "bf16_vs_fp32": quant, "equal_energy": equal,
+                "tim": tim, "sr": sr, "batched": batched,
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clk, "device_error_flags": flags}

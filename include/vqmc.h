@@ -201,8 +201,10 @@ vqmc_status vqmc_sample(vqmc_ctx* ctx, int32_t B, const float* d_u, uint64_t ite
  * of B configurations d_s int8 [B][n].  The diagonal part (Sec. 2.4):
  * E_b = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i.  d_e is int32 [B] (exact)
  * for VQMC_HAM_SPARSE_I32 and float32 [B] otherwise.  The dense kind runs
- * S.J on the tensor cores in BF16 with a hi/lo split of J (error stated in the
- * design notes) in BF16 precision, FP32 otherwise.  With a transverse field
+ * S.J on the tensor cores in BF16 precision, with J split into a BF16 high
+ * part and a BF16 remainder (16 significant bits of every coupling, FP32
+ * accumulation: |E - E_exact| <= n^2 2^-16 max|J_ij|), and on the CUDA cores
+ * in FP32 otherwise (|E - E_exact| <= n^2 2^-23 max|J_ij|).  With a transverse field
  * alpha, also -sum_i alpha_i sqrt(pi(s^(i)) / pi(s)) (s^(i): spin i flipped,
  * Eq. (e:tim)): the n flipped states of every sample and the sample itself
  * go through the model's log-prob GEMMs in chunks of rows, so this costs
@@ -410,9 +412,12 @@ vqmc_status vqmc_timing_read(vqmc_ctx* ctx, double* ms_out, int64_t* steps_out, 
  * spin operand, the hidden activations and the row partial sums) from one
  * static device array of 64 MiB owned by the library instead of the context.
  * It calls no allocating routine.  Limits and caveats:
- *   - the scratch a call needs grows with B, n and h; a call that would need
- *     more than 64 MiB returns VQMC_ERR_UNSUPPORTED with the byte count
- *     (at n = 10,000, h = 2,000 that is about B <= 2,300 in BF16);
+ *   - a call needs r(B np e) + r(B hp e) + r(ceil(n / 128) pad64(B) 4) bytes
+ *     of scratch, with np = pad64(n), hp = pad64(h), e = 2 bytes per element
+ *     in BF16 and 4 in FP32, and r() rounding up to a multiple of 256; a call
+ *     that would need more than 64 MiB (67,108,864 bytes) returns
+ *     VQMC_ERR_UNSUPPORTED with the byte count.  At n = 10,000, h = 2,000
+ *     that allows B <= 2,738 in BF16 and B <= 1,377 in FP32;
  *   - every GPU that loads the library's module holds the 64 MiB until the
  *     process exits;
  *   - the first call on each device looks up the array's device address

@@ -16,11 +16,17 @@
  *   The paper's hidden activation is the rectifier; the logistic sigmoid is
  *   the alternative activation selected with act = 1.
  *
- * Reduced precision (Sec. 4 runs the network in mixed precision; the BF16
- * model of this library is read as: weights rounded to bfloat16, each hidden
- * activation g1_k rounded to bfloat16 before the output layer, everything
- * else exact).  act | VO_HIDDEN_BF16 selects that rounding of g1; the weights
- * are rounded by the caller.
+ * Reduced precision.  The paper states no arithmetic precision; reduced
+ * precision is an option of the library under test, not a step of the
+ * paper's method.  The library's BF16 model is defined here as: weights
+ * rounded to bfloat16, each hidden activation g1_k rounded to bfloat16 before
+ * the output layer, everything else exact.  The library's samplers and its
+ * log-prob/adjoint GEMMs all evaluate this one model, so the score-function
+ * estimator stays unbiased for the distribution that is actually sampled.
+ * act | VO_HIDDEN_BF16 selects the rounding of g1; the weights are rounded by
+ * the caller.  How far this model lies from the exact model of the FP32
+ * master weights (the quantisation error) is measured by the tests against
+ * the exact model (act without VO_HIDDEN_BF16), not assumed.
  *
  * Masks (the paper only asks for "appropriate binary masks", Sec. 2.3; the
  * reading used here is the standard MADE degree rule with sorted degrees):

@@ -69,10 +69,11 @@ template <typename T>
 cudaError_t forward(const vqmc_ctx* c, int B, const int8_t* d_s, float* d_logp, unsigned char* scratch, int ldb,
                     cudaStream_t st) {
   const size_t es = sizeof(T);
+  // scratch layout: spin operand Sx [B][np], hidden activations H [B][hp],
+  // log-pi partial sums [ceil(n/128)][ldb]; each part 256-byte aligned
   T* Sx = reinterpret_cast<T*>(scratch);
   T* H = reinterpret_cast<T*>(scratch + align256((size_t)B * c->np * es));
-  T* Ht = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(H) + align256((size_t)B * c->hp * es));
-  float* part = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(Ht) + align256((size_t)c->h * ldb * es));
+  float* part = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(H) + align256((size_t)B * c->hp * es));
   const int ntiles = (c->n + 127) / 128;
 
   cudaError_t e = launch_spins_to_operands(c, B, d_s, Sx, nullptr, st);
@@ -86,7 +87,7 @@ cudaError_t forward(const vqmc_ctx* c, int B, const int8_t* d_s, float* d_logp, 
   a.Bm = reinterpret_cast<const T*>(c->w_s), a.ldb = c->np;
   a.bias = c->b1;
   a.out = H, a.ldo = c->hp;
-  a.out_t = Ht, a.ldt = ldb;
+  a.out_t = nullptr;  // the transposed activations feed only the adjoint, which this call does not run
   GemmArgs<T> z{};
   z.n = c->n, z.h = c->h, z.act = c->act, z.err = c->err;
   z.op = kOpOut;
@@ -113,7 +114,7 @@ cudaError_t forward(const vqmc_ctx* c, int B, const int8_t* d_s, float* d_logp, 
 size_t noalloc_scratch_bytes(const vqmc_ctx* c, int B) {
   const size_t es = c->prec == VQMC_PREC_BF16 ? 2 : 4;
   const size_t ldb = (size_t)pad_up(B);
-  return align256((size_t)B * c->np * es) + align256((size_t)B * c->hp * es) + align256((size_t)c->h * ldb * es) +
+  return align256((size_t)B * c->np * es) + align256((size_t)B * c->hp * es) +
          align256((size_t)((c->n + 127) / 128) * ldb * 4);
 }
 

@@ -112,3 +112,37 @@ def train(model, batch: int, iters: int = 300, optimizer: str = "adam", lr: floa
 def maxcut_scores(stats, w_tot: float):
     """(mean cut, best cut) of a batch from its energy statistics."""
     return (w_tot - stats[0]) / 2.0, (w_tot - stats[2]) / 2.0
+
+
+def compare_precisions(make_model, batch: int, seeds: int = 5, iters: int = 300, eval_batch: int = 1024,
+                       precisions=("bf16", "fp32")):
+    """Final energies of the same training run at several precisions (Sec. 5.1
+    protocol: `iters` Adam iterations, then the mean energy of an evaluation
+    batch of `eval_batch` fresh samples, averaged over `seeds` runs).
+
+    make_model(precision, seed) must return a fresh vqmc.VQMC with the seed's
+    initial parameters and Philox key, so that for each seed the precisions
+    start from the same state and draw from the same uniform streams.  Also
+    records the evaluation mean before training.  Returns a dict with the
+    per-seed final means per precision, their averages, and the relative
+    difference |mean_a - mean_b| / |mean_b| of the first two precisions."""
+    import torch
+    finals = {p: [] for p in precisions}
+    initial = []
+    for seed in range(seeds):
+        for q, prec in enumerate(precisions):
+            m = make_model(prec, seed)
+            if q == 0:
+                initial.append(evaluate(m, eval_batch, 0)[0])
+            for _ in range(iters):
+                m.step(batch)
+            finals[prec].append(evaluate(m, eval_batch, iters + 1)[0])
+            if m.check() != 0:
+                raise RuntimeError(f"device error flags after the {prec} run of seed {seed}")
+            m.close()
+            del m
+            torch.cuda.empty_cache()
+    means = {p: sum(v) / len(v) for p, v in finals.items()}
+    a, b = precisions[0], precisions[1]
+    return {"seeds": seeds, "iters": iters, "eval_batch": eval_batch, "initial_mean": sum(initial) / len(initial),
+            "final_means": finals, "mean": means, "rel_diff": abs(means[a] - means[b]) / abs(means[b])}

@@ -69,6 +69,92 @@ def teacher_forced(P, S, U, act, tol=1e-6):
     return int(mism.sum()), int((~decided).sum())
 
 
+def _act64(A, act):
+    return np.maximum(A, 0.0) if (act & 1) == oracle.RELU else 1.0 / (1.0 + np.exp(-A))
+
+
+def _to_bf16(x):
+    """FP64 values rounded as the kernels round an FP32 activation: to FP32,
+    then to the nearest bfloat16 (ties to even; torch's conversion)."""
+    f = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
+    return f.to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def bf16_logit_shift(P, S, code):
+    """How far FP32 arithmetic may move the BF16 model's logits from the FP64
+    oracle's, per draw, on the samples S (the oracle's BF16 model P: masked,
+    BF16-valued weights).
+
+    The kernels accumulate each hidden pre-activation a_k in FP32 and round
+    g1_k = act(a_k) to bfloat16.  Where a_k lies within FP32 rounding of the
+    point at which that rounding changes, the kernel's g1_k may be one
+    bfloat16 step away from the oracle's (an "ambiguous" unit), and every
+    later logit z_i moves by |W2_ik| times that step.  FP32 rounding of a_k is
+    taken as 8 * 2^-24 * sqrt(m(k) + 1) * ||(b1_k, W1_k)||_2 (six standard
+    deviations of the rounding noise of an (m(k) + 1)-term sum with terms of
+    mixed sign, plus margin); a sigmoid evaluated in FP32 adds 2^-20 relative.
+    Returns (shift (B, n), ambiguous units per sample (B,))."""
+    W1, b1, W2, b2 = (np.asarray(x, np.float64) for x in P)
+    h, n = W1.shape
+    act = code & 1
+    deg = oracle.degrees(n, h).astype(np.float64)
+    A = np.asarray(S, np.float64) @ W1.T + b1
+    epsA = 8.0 * 2.0 ** -24 * np.sqrt(deg + 1.0) * np.sqrt(np.sum(W1 * W1, axis=1) + b1 * b1)
+    with np.errstate(over="ignore"):
+        lo, hi = _act64(A - epsA, act), _act64(A + epsA, act)
+    if act == oracle.SIGMOID:
+        lo, hi = lo * (1.0 - 2.0 ** -20), hi * (1.0 + 2.0 ** -20)
+    dG = np.abs(_to_bf16(hi) - _to_bf16(lo))
+    return dG @ np.abs(W2).T, (dG > 0).sum(axis=1)
+
+
+def bf16_sample_check(P, S, U, code, lp=None, tie=1e-6):
+    """Teacher-forced check of BF16-model samples S (the GPU's) against the
+    oracle on the same uniforms U.
+
+    A draw is "flagged" when |u - p_i| < tie or when the logit shift of
+    bf16_logit_shift can carry z_i across logit(u).  Every unflagged draw must
+    equal [u < p_i] of the oracle's conditional on the sample's own prefix;
+    flagged draws may go either way and are counted.  Rows in which every
+    draw agrees with the oracle's conditional must equal the free-running
+    oracle's rows on the same uniforms (induction over the steps).  With lp
+    (the sampler's own log pi), every row must lie within sum_i shift_i +
+    1e-5 |log pi| of the oracle's log pi of that row (|d log sigma(s z)/dz| <= 1,
+    plus FP32 accumulation over n terms).  Returns a dict of counts."""
+    S = np.asarray(S)
+    Ud = np.asarray(U, np.float64)
+    Z = oracle.logits(P, S, code)
+    p = sigmoid(Z)
+    shift, namb = bf16_logit_shift(P, S, code)
+    with np.errstate(divide="ignore"):
+        lg = np.log(Ud) - np.log1p(-Ud)
+    near = np.abs(Ud - p) < tie
+    flagged = near | (np.abs(lg - Z) <= shift)
+    wrong = (S == 1) != (Ud < p)
+    out = {
+        "draws": int(S.size),
+        "near_ties_1e-6": int(near.sum()),
+        "band_1e-6_1e-4": int(((np.abs(Ud - p) >= tie) & (np.abs(Ud - p) < 1e-4)).sum()),
+        "ambiguous_units_mean": float(namb.mean()) if namb.size else 0.0,
+        "flagged": int(flagged.sum()),
+        "flagged_other_way": int((wrong & flagged).sum()),
+        "unflagged_mismatches": int((wrong & ~flagged).sum()),
+    }
+    clean = ~wrong.any(axis=1)
+    So, _ = oracle.sample(P, Ud.astype(np.float32), code)
+    out["rows"] = int(S.shape[0])
+    out["rows_equal_free_running"] = int((S == So).all(axis=1).sum())
+    out["rows_with_flagged_other_way"] = int((~clean).sum())
+    out["clean_rows_equal"] = bool(np.array_equal(S[clean], So[clean]))
+    if lp is not None:
+        lpo = oracle.logprob(P, S, code)
+        bound = shift.sum(axis=1) + 1e-5 * np.abs(lpo)
+        err = np.abs(np.asarray(lp, np.float64) - lpo)
+        out["logp_within_bound"] = bool(np.all(err <= bound))
+        out["logp_max_rel"] = float(np.max(err / np.maximum(np.abs(lpo), 1e-30)))
+    return out
+
+
 def rows_without_near_ties(P, S_oracle, U, act, tol=1e-6):
     Z = oracle.logits(P, S_oracle, act_code(act))
     return ~(np.abs(np.asarray(U, np.float64) - sigmoid(Z)) < tol).any(axis=1)

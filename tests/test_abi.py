@@ -128,3 +128,18 @@ def test_batch_rejects_bad_arguments(lib):
     assert lib.vqmc_batch_count(None) == 0
     assert not lib.vqmc_batch_member(None, 0)
     assert lib.vqmc_batch_step(None, None, None, None) == vqmc.VQMC_ERR_INVALID_ARG
+
+
+def test_noalloc_source_calls_no_allocating_routine():
+    """The allocation-free entry point's translation unit calls no
+    cudaMalloc*/cudaFree* routine (comments aside) and takes its scratch from
+    the file-scope __device__ array, whose address it looks up with
+    cudaGetSymbolAddress."""
+    import re
+    src = open(os.path.join(ROOT, "paper_2106_13308_gb300", "csrc", "noalloc.cu")).read()
+    code = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    code = re.sub(r"//[^\n]*", "", code)
+    assert not re.search(r"\bcuda(Malloc|Free)\w*\s*\(", code)
+    assert not re.search(r"\bcuMem(Alloc|Free)\w*\s*\(", code)
+    assert re.search(r"static\s+__device__\s+__align__\(256\)", code)
+    assert "cudaGetSymbolAddress" in code

@@ -1,18 +1,25 @@
 """GPU parity: every step of the hot path through the C ABI against the FP64
 oracle, element by element, on seeded inputs.
 
-Tolerances (written here, derived in the design notes):
-  * uniforms, samples on shared uniforms, integer energies: bit-exact
-    (samples exclude near-ties |u - p_i| < 1e-6 with FP32 weights, which are
-    counted; 1e-4 for the BF16 model, where a hidden activation whose FP32
-    pre-activation lies within FP32 rounding of a BF16 rounding boundary may
-    round the other way than in FP64 and move later logits by up to
-    |W2_ik| 2^-8 |g1_k|); the sampler's log pi: relative 1e-5 (FP32), 1e-3
-    (BF16 model, for the same reason);
+Tolerances:
+  * uniforms, samples on shared uniforms, integer energies: bit-exact.
+    Samples are checked teacher-forced: every draw with |u - p_i| >= 1e-6
+    must equal [u < p_i] of the oracle's conditional on the sample's own
+    prefix.  For the BF16 model a draw is also exempt when a hidden unit that
+    feeds its logit has an FP32 pre-activation within FP32 rounding of a
+    bfloat16 rounding boundary (the kernel's g1_k may then be one bfloat16
+    step from the oracle's) and that step, times |W2_ik|, can carry z_i
+    across logit(u) (gpu_helpers.bf16_logit_shift).  Exempt draws are counted
+    and reported, with the draws in 1e-6 <= |u - p_i| < 1e-4 and the rows that
+    differ from the free-running oracle;
+  * the sampler's log pi: relative 1e-5 with FP32 weights; BF16: within the
+    sum over draws of that logit shift plus 1e-5 relative;
   * log pi: relative error <= 1e-5 with FP32 weights and <= 2e-2 with BF16
     weights (the oracle then runs the BF16 model: the same BF16-rounded
     weights and bfloat16-rounded hidden activations);
-  * gradients: ||g - g_ref|| / ||g_ref|| <= 1e-4 (FP32), <= 3e-2 (BF16);
+  * gradients: ||g - g_ref|| / ||g_ref|| <= 1e-4 (FP32), <= 3e-2 (BF16: the
+    GEMM operands H, delta and the hidden adjoint are BF16, 2^-9 relative
+    each, through three GEMMs), each parameter block within 3x that;
   * FP64 statistics given identical energies: relative 1e-12.
 """
 import numpy as np
@@ -22,8 +29,9 @@ import torch
 import oracle
 from paper_2106_13308_gb300 import inputs
 
-from gpu_helpers import (ACT_ORACLE, act_code, build_lib, grad_blocks, logp_rel, make_model, masked, oracle_params,
-                         rel_err, rows_without_near_ties, teacher_forced, er_instance)
+from conftest import report
+from gpu_helpers import (ACT_ORACLE, act_code, bf16_sample_check, build_lib, grad_blocks, logp_rel, make_model, masked,
+                         oracle_params, rel_err, rows_without_near_ties, teacher_forced, er_instance)
 
 pytestmark = pytest.mark.gpu
 
@@ -68,26 +76,28 @@ def test_sampler_matches_oracle(n, h, B, act, prec, p):
     S, lp = S.cpu().numpy(), lp.cpu().numpy()
     assert set(np.unique(S)) <= {-1, 1}
     # teacher-forced: each spin decided by the oracle's conditional on its own prefix
-    _check_samples(P, S, lp, U, act_code(act, prec), prec)
+    _check_samples(P, S, lp, U, act_code(act, prec), prec, f"n={n} h={h} B={B} {act}")
 
 
-def _check_samples(P, S, lp, U, code, prec):
-    tol = TIE[prec]
-    mism, ties = teacher_forced(P, S, U, code, tol)
-    assert mism == 0, (mism, ties)
-    # free-running oracle on the same uniforms: identical rows (barring near-ties)
-    So, lpo = oracle.sample(P, U, code)
-    rows = rows_without_near_ties(P, So, U, code, tol)
-    B = S.shape[0]
-    assert rows.sum() >= (B - 2 if prec == "fp32" else B // 2), (rows.sum(), B)
-    assert np.array_equal(S[rows], So[rows])
-    assert logp_rel(lp[rows], lpo[rows]) <= LOGP_SAMPLER[prec]
-
-
-TIE = {"fp32": 1e-6, "bf16": 1e-4}
-# log pi accumulated by the sampler; one BF16 hidden activation rounding the
-# other way moves it by at most sum_i |W2_ik| 2^-8 |g1_k|
-LOGP_SAMPLER = {"fp32": 1e-5, "bf16": 1e-3}
+def _check_samples(P, S, lp, U, code, prec, label=""):
+    if prec == "fp32":
+        mism, ties = teacher_forced(P, S, U, code, 1e-6)
+        assert mism == 0, (mism, ties)
+        # free-running oracle on the same uniforms: identical rows (barring near-ties)
+        So, lpo = oracle.sample(P, U, code)
+        rows = rows_without_near_ties(P, So, U, code, 1e-6)
+        B = S.shape[0]
+        assert rows.sum() >= B - 2, (rows.sum(), B)
+        assert np.array_equal(S[rows], So[rows])
+        assert logp_rel(lp[rows], lpo[rows]) <= 1e-5
+        report(f"samples fp32 {label}", draws=int(S.size), near_ties_1e6=ties, rows=int(B),
+               rows_equal_free_running=int((S == So).all(axis=1).sum()))
+        return
+    c = bf16_sample_check(P, S, U, code, lp=lp)
+    report(f"samples bf16 {label}", **c)
+    assert c["unflagged_mismatches"] == 0, c
+    assert c["clean_rows_equal"], c
+    assert c["logp_within_bound"], c
 
 # Models where the tensor-core sampler applies (at most 32 hidden units
 # completing within a block of 128, or of 64, steps): ragged n and B.
@@ -110,13 +120,16 @@ def test_tensor_core_sampler_matches_oracle(n, h, B, act, p):
     S, lp = m.sample(B, torch.from_numpy(U).cuda())
     S, lp = S.cpu().numpy(), lp.cpu().numpy()
     assert set(np.unique(S)) <= {-1, 1}
-    _check_samples(P, S, lp, U, act_code(act, "bf16"), "bf16")
+    _check_samples(P, S, lp, U, act_code(act, "bf16"), "bf16", f"tensor-core n={n} h={h} B={B} {act}")
     assert m.check() == 0
-    # the CUDA-core sampler runs the same model: same rows barring near-ties
+    # the CUDA-core sampler runs the same model: the same check, and the rows
+    # of the two samplers compared
     c = make_model(n, h, B, inst, act=act, precision="bf16", theta=theta, sampler="cuda_core")
     S2, lp2 = c.sample(B, torch.from_numpy(U).cuda())
-    same = (S2.cpu().numpy() == S).all(axis=1)
-    assert same.sum() >= B // 2
+    S2, lp2 = S2.cpu().numpy(), lp2.cpu().numpy()
+    _check_samples(P, S2, lp2, U, act_code(act, "bf16"), "bf16", f"cuda-core n={n} h={h} B={B} {act}")
+    report(f"tensor-core vs cuda-core rows n={n} h={h} B={B}", rows=int(B),
+           rows_equal=int((S2 == S).all(axis=1).sum()))
 
 
 def test_tensor_core_sampler_internal_philox_and_steps():
@@ -131,7 +144,7 @@ def test_tensor_core_sampler_internal_philox_and_steps():
     for it in (0, 3):
         S, lp = m.sample(B, None, iteration=it)
         U = oracle.uniforms(B, n, seed, it)
-        _check_samples(P, S.cpu().numpy(), lp.cpu().numpy(), U, code, "bf16")
+        _check_samples(P, S.cpu().numpy(), lp.cpu().numpy(), U, code, "bf16", f"tensor-core Philox it={it}")
     assert m.check() == 0
 
 

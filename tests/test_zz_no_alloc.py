@@ -6,8 +6,11 @@ array shared by all calls.
 
 Called through the C ABI (ctypes) and compared with vqmc_logprob on two calls
 in a row with different spins, at the tolerance the log-prob parity tests use
-(relative 1e-5).  This file is named to be collected last, and it passes both
-alone in a fresh process and after the other tests.
+(relative 1e-5), and at the edge of the scratch limit: the largest batch whose
+scratch (the size formula stated in include/vqmc.h) fits in the 64 MiB is
+accepted and matches, and one padding step more (64 samples) is refused.
+This file is named to be collected last, and it passes both alone in a fresh
+process and after the other tests.
 """
 import ctypes
 
@@ -76,3 +79,34 @@ def test_noalloc_rejects_batches_beyond_the_static_scratch(vq):
     torch.cuda.synchronize()
     r, o = ref.cpu().numpy().astype(np.float64), out[:b].cpu().numpy().astype(np.float64)
     assert np.max(np.abs(o - r) / np.abs(r)) <= 1e-5
+
+
+def _scratch_bytes(B, n, h, es):
+    """The scratch a call needs, as include/vqmc.h states it."""
+    r = lambda x: (x + 255) // 256 * 256  # noqa: E731
+    p64 = lambda x: (x + 63) // 64 * 64  # noqa: E731
+    return r(B * p64(n) * es) + r(B * p64(h) * es) + r(((n + 127) // 128) * p64(B) * 4)
+
+
+def test_noalloc_at_the_edge_of_the_scratch_limit(vq):
+    limit = 64 << 20
+    n, h = 1000, 512
+    B = 1
+    while _scratch_bytes(B + 1, n, h, 2) <= limit:
+        B += 1
+    assert _scratch_bytes(B, n, h, 2) <= limit < _scratch_bytes(B + 64, n, h, 2)
+    m = _model(vq, n, h, B + 64, "bf16", 61)
+    lib = vq.load_library()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    S = torch.from_numpy(inputs.spins(B + 64, n, 62)).cuda()
+    out = torch.full((B + 64,), float("nan"), dtype=torch.float32, device="cuda")
+    st = lib.vqmc_logprob_noalloc(m.ctx, B, ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(out.data_ptr()), stream)
+    assert st == vq.VQMC_OK, lib.vqmc_last_error()
+    ref = m.logprob(S[:B])
+    torch.cuda.synchronize()
+    r, o = ref.cpu().numpy().astype(np.float64), out[:B].cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(o - r) / np.abs(r)) <= 1e-5
+    st = lib.vqmc_logprob_noalloc(m.ctx, B + 64, ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  stream)
+    assert st == vq.VQMC_ERR_UNSUPPORTED
+    assert m.check() == 0
