@@ -308,6 +308,56 @@ vqmc_status vqmc_graph_capture(vqmc_ctx* ctx, int32_t B, int32_t steps, int32_t 
  * nothing was captured. */
 vqmc_status vqmc_graph_launch(vqmc_ctx* ctx, vqmc_stream stream, vqmc_step_stats* h_out);
 
+/* Sampling parallelism over GPUs (Sec. 4, "Sampling Parallelization"; the
+ * multi-GPU runs of Sec. 5.4 and Tables 6-7).  The samples of an iteration
+ * are independent draws from the same model, so L GPUs, each with its own
+ * context holding the same parameters, draw disjoint shards of one batch of
+ * B_tot samples and exchange one set of sums per iteration.  For any
+ * constant c (the `shift`, the same on every rank) and g_b = grad log pi(s_b),
+ *     sum_b (E_b - Ebar) g_b = sum_b (E_b - c) g_b - (Ebar - c) sum_b g_b,
+ * so each rank writes S1 = sum_{b in shard} (E_b - c) g_b and
+ * S0 = sum_{b in shard} g_b (float32, 2d values) and the FP64 scalars
+ * {sum (E_b - c), sum (E_b - c)^2, B}; one element-wise sum of these over the
+ * ranks (an all-reduce, done by the caller: NCCL, MPI or host code) lets
+ * every rank form the exact global-baseline gradient
+ * (1/B_tot) sum_b (E_b - Ebar) g_b of the whole batch (Sec. 2.1) and apply
+ * the same Adam step, so the replicas stay identical.  A shift near Ebar
+ * (for example the previous iteration's global mean) keeps the FP32 sums
+ * well conditioned; 0 gives the plain sums. */
+
+/* Index of this context's sample 0 in the Philox counter (default 0): the
+ * internal uniforms of sample b are those of global sample b0 + b, so ranks
+ * with offsets 0, B, 2B, ... draw disjoint streams whose union is the batch
+ * one context with max_batch = B_tot would draw.  b0 + B must stay below
+ * 2^32.  Affects vqmc_sample with d_u = NULL, vqmc_uniforms, vqmc_step and
+ * vqmc_shard_sums; takes effect for calls enqueued after it. */
+vqmc_status vqmc_set_sample_offset(vqmc_ctx* ctx, uint32_t b0);
+
+/* This shard's sums.  d_s = NULL: draws B samples with the internal uniforms
+ * of the context's iteration counter (and sample offset) and their local
+ * energies into the context's batch buffers (vqmc_last_batch), as vqmc_step
+ * does; otherwise uses d_s int8 [B][n] and d_e (int32/float32 [B] per
+ * instance kind).  Writes d_sums float32 [2d] = [S1 | S0] (theta layout
+ * each, zero outside the masks) and d_scalars double [3] =
+ * {sum (E_b - shift), sum (E_b - shift)^2, B}.  Costs one hidden-activation
+ * GEMM and two adjoint passes.  B = 0 writes zeros.  Errors: INVALID_ARG
+ * (null outputs, d_s without d_e, non-finite shift), those of the kernels;
+ * a non-finite energy sets VQMC_DEVERR_NONFINITE. */
+vqmc_status vqmc_shard_sums(vqmc_ctx* ctx, int32_t B, const int8_t* d_s, const void* d_e, double shift, float* d_sums,
+                            double* d_scalars, vqmc_stream stream);
+
+/* The update from the sums of all ranks (d_sums [2d], d_scalars [3], summed
+ * element-wise over the ranks; shift as given to vqmc_shard_sums): forms the
+ * gradient (S1 - (Ebar - shift) S0) / B_tot with Ebar - shift =
+ * sum (E_b - shift) / B_tot, writes it to d_grad [d] (NULL: the context's own
+ * buffer), writes d_stats double [2] = {Ebar, variance with 1/B_tot} (NULL
+ * allowed), applies one Adam step and advances the iteration counter.  Every
+ * rank that passes the same sums applies the same update.  A total count
+ * below 1 or non-finite scalars give a zero gradient and set
+ * VQMC_DEVERR_NONFINITE. */
+vqmc_status vqmc_shard_apply(vqmc_ctx* ctx, const float* d_sums, const double* d_scalars, double shift, float* d_grad,
+                             double* d_stats, vqmc_stream stream);
+
 /* A batch of independent problems (each member an ordinary context with its
  * own model, instance, optimiser and workspaces), stepped together: many
  * Max-Cut instances of different sizes trained at once, so that small

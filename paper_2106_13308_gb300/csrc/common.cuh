@@ -93,6 +93,10 @@ struct vqmc_ctx {
   uint64_t inst_hash = 0;
   int device;
   int num_sms;
+  // index of this context's sample 0 in the Philox counter: 0, or the first
+  // global sample of the shard this context draws (vqmc_set_sample_offset)
+  uint32_t sample_offset = 0;
+  float* ones = nullptr;  // [Bmax] unit coefficients (the shard sums' sum of scores)
 
   // FP32 master parameters, optimiser state, gradient (d floats each)
   float* theta = nullptr;
@@ -189,7 +193,9 @@ struct vqmc_ctx {
 namespace vqmc {
 
 // ---- sampler.cu
-cudaError_t launch_uniforms(int B, int n, uint64_t seed, uint64_t iteration, float* d_u, cudaStream_t st);
+// boff: index of sample 0 in the Philox counter
+cudaError_t launch_uniforms(int B, int n, uint64_t seed, uint64_t iteration, float* d_u, cudaStream_t st,
+                            uint32_t boff = 0);
 // it_dev: when not null, the Philox iteration is read from it on the device
 // (the context's DevState) instead of `iteration`
 cudaError_t launch_sampler(const vqmc_ctx* c, int B, const float* d_u, uint64_t iteration, int8_t* d_s,

@@ -5,8 +5,9 @@
 // instantiated in sampler_bf16.cu and sampler_f32.cu) for every other model.
 //
 // uniforms_kernel writes the same stream the samplers draw internally:
-// u_{b,i} = word (i mod 4) of Philox4x32-10(counter (i/4, b, iteration),
-// key = seed), as (x >> 8) 2^-24.
+// u_{b,i} = word (i mod 4) of Philox4x32-10(counter (i/4, b0 + b, iteration),
+// key = seed), as (x >> 8) 2^-24, with b0 the context's sample offset (0
+// unless the context draws one shard of a batch spread over several GPUs).
 #include <cstdio>
 
 #include "sampler.cuh"
@@ -14,14 +15,14 @@
 namespace vqmc {
 namespace {
 
-__global__ void uniforms_kernel(int B, int n, uint32_t k0, uint32_t k1, uint32_t it0, uint32_t it1,
+__global__ void uniforms_kernel(int B, int n, uint32_t k0, uint32_t k1, uint32_t it0, uint32_t it1, uint32_t boff,
                                 float* __restrict__ u) {
   const int groups = (n + 3) / 4;
   const long long tot = (long long)B * groups;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot;
        q += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(q / groups), g = (int)(q % groups);
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)b, it0, it1), k0, k1);
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)b + boff, it0, it1), k0, k1);
     const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -33,12 +34,13 @@ __global__ void uniforms_kernel(int B, int n, uint32_t k0, uint32_t k1, uint32_t
 
 }  // namespace
 
-cudaError_t launch_uniforms(int B, int n, uint64_t seed, uint64_t iteration, float* d_u, cudaStream_t st) {
+cudaError_t launch_uniforms(int B, int n, uint64_t seed, uint64_t iteration, float* d_u, cudaStream_t st,
+                            uint32_t boff) {
   if (B <= 0 || n <= 0) return cudaSuccess;
   const long long work = (long long)B * ((n + 3) / 4);
   const int grid = (int)((work + 255) / 256 < 4096 ? (work + 255) / 256 : 4096);
   uniforms_kernel<<<grid, 256, 0, st>>>(B, n, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)iteration,
-                                        (uint32_t)(iteration >> 32), d_u);
+                                        (uint32_t)(iteration >> 32), boff, d_u);
   return cudaGetLastError();
 }
 
@@ -61,6 +63,7 @@ cudaError_t launch_sampler(const vqmc_ctx* c, int B, const float* d_u, uint64_t 
   a.key1 = (uint32_t)(c->cfg.seed >> 32);
   a.it0 = (uint32_t)iteration;
   a.it1 = (uint32_t)(iteration >> 32);
+  a.boff = c->sample_offset;
   a.it_dev = it_dev;
   a.s_out = d_s;
   a.logp = d_logp;

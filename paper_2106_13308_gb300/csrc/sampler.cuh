@@ -16,6 +16,7 @@ struct SamplerArgs {
   const float* b2;  // [n]
   const float* u;   // [B][n] or null (internal Philox)
   uint32_t key0, key1, it0, it1;
+  uint32_t boff;    // index of sample 0 in the Philox counter (a shard's first global sample)
   const unsigned long long* it_dev;  // if not null: the Philox iteration, read on the device
   int8_t* s_out;    // [B][n]
   float* logp;      // [B] or null

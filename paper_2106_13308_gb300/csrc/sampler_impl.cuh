@@ -360,7 +360,7 @@ struct Run {
         for (int e = 0; e < 4; ++e) uw[e] = logit(unx[e]);
         if (t + UWIN < n) load_u(t + UWIN, unx);
       } else {
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)((t + 4 * ug) >> 2), (uint32_t)ub, it0, it1), g.key0,
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)((t + 4 * ug) >> 2), (uint32_t)ub + g.boff, it0, it1), g.key0,
                                       g.key1);
         uw[0] = logit(to_unit(r.x)), uw[1] = logit(to_unit(r.y));
         uw[2] = logit(to_unit(r.z)), uw[3] = logit(to_unit(r.w));

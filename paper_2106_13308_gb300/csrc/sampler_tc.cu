@@ -89,6 +89,7 @@ struct TcArgs {
   const float* b2;
   const float* u;     // [B][n] or null (internal Philox)
   uint32_t key0, key1, it0, it1;
+  uint32_t boff;      // index of sample 0 in the Philox counter (a shard's first global sample)
   const unsigned long long* it_dev;  // if not null: the Philox iteration, read on the device
   int8_t* s_out;      // [B][n]
   float* logp;        // [B] or null
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int w = 0; w < 4; ++w)
             dst[w * kS] = (bb < g.B && t + w < n) ? logit(__ldg(g.u + (size_t)bb * n + t + w)) : 0.0f;
         } else {
-          const uint4 r = philox4x32_10(make_uint4((uint32_t)(t >> 2), (uint32_t)bb, it0, it1), g.key0, g.key1);
+          const uint4 r = philox4x32_10(make_uint4((uint32_t)(t >> 2), (uint32_t)bb + g.boff, it0, it1), g.key0, g.key1);
           dst[0] = logit(to_unit(r.x));
           dst[kS] = logit(to_unit(r.y));
           dst[2 * kS] = logit(to_unit(r.z));
@@ -749,6 +750,7 @@ cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64
   a.key1 = (uint32_t)(c->cfg.seed >> 32);
   a.it0 = (uint32_t)iteration;
   a.it1 = (uint32_t)(iteration >> 32);
+  a.boff = c->sample_offset;
   a.it_dev = it_dev;
   a.s_out = d_s;
   a.logp = d_logp;

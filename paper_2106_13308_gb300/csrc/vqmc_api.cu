@@ -283,6 +283,12 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
   VQ_ALLOC(c->GAt, (size_t)h * c->Bp * es);
   VQ_ALLOC(c->logp, (size_t)Bmax * 4);
   VQ_ALLOC(c->coef, (size_t)Bmax * 4);
+  VQ_ALLOC(c->ones, (size_t)Bmax * 4);
+  {
+    const std::vector<float> one((size_t)Bmax, 1.0f);
+    if (cudaMemcpy(c->ones, one.data(), (size_t)Bmax * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup_fail(VQMC_ERR_CUDA, "copy of the unit coefficients failed");
+  }
   VQ_ALLOC(c->stats, 8 * sizeof(double));
   c->row_part_tiles = (n + 127) / 128;
   c->row_part_ld = c->Bp;
@@ -398,7 +404,7 @@ void vqmc_destroy(vqmc_ctx* c) {
                   c->D, c->Dt, c->GAt, c->logp, c->coef, c->stats, c->row_part, c->col_part, c->err,
                   c->step_stats, c->Sbits, c->eloc_part, c->eloc_slice, c->erow, c->alpha, c->tim_A,
                   c->tim_S8, c->tim_H, c->tim_row_part, c->sr_A, c->sr_x, c->sr_ones, c->sr_xinv,
-                  c->sr_events, c->dstate};
+                  c->sr_events, c->dstate, c->ones};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -443,7 +449,7 @@ vqmc_status vqmc_uniforms(vqmc_ctx* c, int32_t B, uint64_t iteration, float* d_u
   vqmc_status s = check_B(c, B);
   if (s != VQMC_OK) return s;
   if (B > 0 && !d_u) return fail(VQMC_ERR_INVALID_ARG, "null output");
-  VQ_CUDA(launch_uniforms(B, c->n, c->cfg.seed, iteration, d_u, S(stream)));
+  VQ_CUDA(launch_uniforms(B, c->n, c->cfg.seed, iteration, d_u, S(stream), c->sample_offset));
   return VQMC_OK;
 }
 
@@ -628,6 +634,137 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
     const int energy = !sparse ? 2 : (tc ? 0 : 1) + 1 + (c->eloc_slices > 1 ? 1 : 0);
     c->launches += sampler + energy + tim_launches + 1 + 7 + (fuse ? 1 : 2) + (tc ? 2 : 0) + 1;
   }
+  c->iter += 1;
+  return VQMC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------- sampling parallelism
+//
+// Sec. 4: the samples of one iteration are independent, so L GPUs draw
+// disjoint shards of the batch (each context's sample offset places its
+// samples in the Philox counter) and combine their gradients.  With the
+// global mean Ebar over all B_tot samples,
+//     sum_b (E_b - Ebar) g_b = sum_b (E_b - c) g_b - (Ebar - c) sum_b g_b
+// for any constant c, g_b = grad log pi(s_b): each shard writes the two
+// d-vectors on the right and the FP64 sums of E_b - c and (E_b - c)^2; one
+// all-reduce (sum) of those gives every replica the exact global-baseline
+// gradient, and identical Adam steps keep the replicas identical.
+
+namespace {
+
+template <typename T>
+__global__ void shard_coef_kernel(int B, const T* __restrict__ e, double shift, float* __restrict__ c1,
+                                  double* __restrict__ scal, uint32_t* err) {
+  __shared__ double s1[256], s2[256];
+  const int tid = threadIdx.x;
+  double a = 0.0, q = 0.0;
+  bool bad = false;
+  for (int b = tid; b < B; b += 256) {
+    const double x = (double)e[b] - shift;
+    bad |= !isfinite(x);
+    c1[b] = (float)x;
+    a += x;
+    q += x * x;
+  }
+  s1[tid] = a, s2[tid] = q;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {  // fixed order: bit-reproducible sums
+    if (tid < w) s1[tid] += s1[tid + w], s2[tid] += s2[tid + w];
+    __syncthreads();
+  }
+  if (bad) atomicOr(err, kErrNonfinite);
+  if (tid == 0) scal[0] = s1[0], scal[1] = s2[0], scal[2] = (double)B;
+}
+
+// grad = (S1 - (Ebar - c) S0) / B_tot from the reduced sums; block 0 writes
+// the FP64 statistics {mean, var} and advances the Philox iteration
+__global__ void shard_grad_kernel(long long d, const float* __restrict__ sums, const double* __restrict__ scal,
+                                  double shift, float* __restrict__ grad, double* __restrict__ stats, DevState* ds,
+                                  uint32_t* err) {
+  const double Bt = scal[2];
+  const bool ok = Bt >= 1.0 && isfinite(scal[0]) && isfinite(scal[1]);
+  const double m = ok ? scal[0] / Bt : 0.0;  // Ebar - c
+  const float a = (float)m, inv = ok ? (float)(1.0 / Bt) : 0.0f;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < d; j += (long long)gridDim.x * blockDim.x)
+    grad[j] = fmaf(-a, sums[d + j], sums[j]) * inv;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!ok) atomicOr(err, kErrNonfinite);
+    if (stats) stats[0] = shift + m, stats[1] = ok ? scal[1] / Bt - m * m : 0.0;
+    ds->iter += 1;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+vqmc_status vqmc_set_sample_offset(vqmc_ctx* c, uint32_t b0) {
+  if (!c) return fail(VQMC_ERR_INVALID_ARG, "null context");
+  c->sample_offset = b0;
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_shard_sums(vqmc_ctx* c, int32_t B, const int8_t* d_s, const void* d_e, double shift, float* d_sums,
+                            double* d_scalars, vqmc_stream stream) {
+  vqmc_status s = check_B(c, B);
+  if (s != VQMC_OK) return s;
+  if (!d_sums || !d_scalars) return fail(VQMC_ERR_INVALID_ARG, "null output");
+  if (!std::isfinite(shift)) return fail(VQMC_ERR_INVALID_ARG, "shift must be finite");
+  if (d_s && !d_e) return fail(VQMC_ERR_INVALID_ARG, "samples given without their energies");
+  cudaStream_t st = S(stream);
+  if (B == 0) {
+    VQ_CUDA(cudaMemsetAsync(d_sums, 0, (size_t)c->d * 8, st));
+    VQ_CUDA(cudaMemsetAsync(d_scalars, 0, 3 * sizeof(double), st));
+    return VQMC_OK;
+  }
+  const bool sparse = c->ham != VQMC_HAM_DENSE_F32;
+  if (!d_s) {
+    // this shard's samples (internal Philox at the iteration counter, from
+    // the sample offset) and their local energies, as in vqmc_step
+    const bool tc = c->sampler == VQMC_SAMPLER_TENSOR_CORE;
+    const unsigned long long* it_dev = &c->dstate->iter;
+    if (tc)
+      VQ_CUDA(launch_sampler_tc(c, B, nullptr, c->iter, c->S, nullptr, st, c->Sx, c->St, sparse ? c->Sbits : nullptr,
+                                it_dev));
+    else {
+      VQ_CUDA(launch_sampler(c, B, nullptr, c->iter, c->S, nullptr, st, it_dev));
+      VQ_CUDA(launch_spins_to_operands(c, B, c->S, c->Sx, c->St, st));
+    }
+    if (sparse) {
+      VQ_CUDA(launch_eloc_sparse(c, B, c->S, c->E, st, /*packed=*/tc));
+    } else {
+      VQ_CUDA(launch_gemm(c, kOpEloc, B, c->S, nullptr, nullptr, st));
+      VQ_CUDA(launch_eloc_dense_finish(c, B, c->S, c->E, st));
+    }
+    VQ_CUDA(launch_tim_offdiag(c, B, c->S, (float*)c->E, st));
+    d_s = c->S, d_e = c->E;
+  } else {
+    VQ_CUDA(launch_spins_to_operands(c, B, d_s, c->Sx, c->St, st));
+  }
+  if (c->ham == VQMC_HAM_SPARSE_I32)
+    shard_coef_kernel<int32_t><<<1, 256, 0, st>>>(B, (const int32_t*)d_e, shift, c->coef, d_scalars, c->err);
+  else
+    shard_coef_kernel<float><<<1, 256, 0, st>>>(B, (const float*)d_e, shift, c->coef, d_scalars, c->err);
+  VQ_CUDA(cudaGetLastError());
+  s = backward_from_operands(c, B, d_s, c->coef, d_sums, st);
+  if (s != VQMC_OK) return s;
+  return backward_from_operands(c, B, d_s, c->ones, d_sums + c->d, st, nullptr, /*hidden_done=*/true);
+}
+
+vqmc_status vqmc_shard_apply(vqmc_ctx* c, const float* d_sums, const double* d_scalars, double shift, float* d_grad,
+                             double* d_stats, vqmc_stream stream) {
+  if (!c) return fail(VQMC_ERR_INVALID_ARG, "null context");
+  if (!d_sums || !d_scalars) return fail(VQMC_ERR_INVALID_ARG, "null argument");
+  if (!std::isfinite(shift)) return fail(VQMC_ERR_INVALID_ARG, "shift must be finite");
+  cudaStream_t st = S(stream);
+  float* g = d_grad ? d_grad : c->grad;
+  const long long work = (c->d + 255) / 256;
+  const int grid = (int)std::min<long long>(work, 8LL * c->num_sms);
+  shard_grad_kernel<<<grid, 256, 0, st>>>(c->d, d_sums, d_scalars, shift, g, d_stats, c->dstate, c->err);
+  VQ_CUDA(cudaGetLastError());
+  VQ_CUDA(launch_adam(c, g, st));
   c->iter += 1;
   return VQMC_OK;
 }

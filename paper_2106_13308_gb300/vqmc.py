@@ -38,7 +38,8 @@ EXPORTS = [
     "vqmc_timing_read", "vqmc_logprob_noalloc", "vqmc_last_error", "vqmc_batch_create", "vqmc_batch_destroy",
     "vqmc_batch_count", "vqmc_batch_member", "vqmc_batch_step", "vqmc_sr_gram", "vqmc_sr_direction",
     "vqmc_sr_step", "vqmc_graph_capture", "vqmc_graph_launch", "vqmc_batch_graph_capture",
-    "vqmc_batch_graph_launch", "vqmc_batch_autotune",
+    "vqmc_batch_graph_launch", "vqmc_batch_autotune", "vqmc_set_sample_offset", "vqmc_shard_sums",
+    "vqmc_shard_apply",
 ]
 OPT = {"adam": 0, "sr": 1}
 PARTS = ["sample", "energy", "stats", "grad", "adam"]
@@ -108,6 +109,9 @@ def load_library(path: str = LIB_PATH):
         "vqmc_timing_enable": (st, [P, ctypes.c_int]),
         "vqmc_timing_read": (st, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "vqmc_logprob_noalloc": (st, [P, I32, P, P, P]),
+        "vqmc_set_sample_offset": (st, [P, ctypes.c_uint32]),
+        "vqmc_shard_sums": (st, [P, I32, P, P, ctypes.c_double, P, P, P]),
+        "vqmc_shard_apply": (st, [P, P, P, ctypes.c_double, P, P, P]),
         "vqmc_last_error": (ctypes.c_char_p, []),
         "vqmc_batch_create": (st, [ctypes.POINTER(Config), ctypes.POINTER(Instance), I32, ctypes.POINTER(P)]),
         "vqmc_batch_destroy": (None, [P]),
@@ -225,6 +229,20 @@ def vqmc_adam(ctx, grad, stream=None):
 
 def vqmc_step(ctx, B: int, out: StepStats | None = None, stream=None):
     _check(load_library().vqmc_step(ctx, B, _stream(stream), ctypes.byref(out) if out is not None else None))
+
+
+def vqmc_set_sample_offset(ctx, b0: int):
+    _check(load_library().vqmc_set_sample_offset(ctx, int(b0)))
+
+
+def vqmc_shard_sums(ctx, B: int, s, e, shift: float, sums, scalars, stream=None):
+    _check(load_library().vqmc_shard_sums(ctx, B, _ptr(s), _ptr(e), float(shift), _ptr(sums), _ptr(scalars),
+                                          _stream(stream)))
+
+
+def vqmc_shard_apply(ctx, sums, scalars, shift: float, grad=None, stats=None, stream=None):
+    _check(load_library().vqmc_shard_apply(ctx, _ptr(sums), _ptr(scalars), float(shift), _ptr(grad), _ptr(stats),
+                                           _stream(stream)))
 
 
 def vqmc_sr_gram(ctx, B: int, s, gram, stream=None):
@@ -411,6 +429,25 @@ class VQMC:
     def step(self, B, out: StepStats | None = None):
         vqmc_step(self.ctx, B, out)
         return out
+
+    # sampling parallelism: one shard of a batch spread over several GPUs
+    def set_sample_offset(self, b0):
+        vqmc_set_sample_offset(self.ctx, b0)
+
+    def shard_sums(self, B, shift=0.0, s=None, e=None):
+        """(sums float32 [2d], scalars float64 [3]) of this shard; with s = None
+        the shard's samples are drawn (internal Philox, sample offset)."""
+        sums = torch.empty(2 * self.d, dtype=torch.float32, device="cuda")
+        scal = torch.empty(3, dtype=torch.float64, device="cuda")
+        vqmc_shard_sums(self.ctx, B, s, e, shift, sums, scal)
+        return sums, scal
+
+    def shard_apply(self, sums, scalars, shift=0.0):
+        """Gradient from the all-ranks sums, one Adam step; returns (grad, stats)."""
+        g = torch.empty(self.d, dtype=torch.float32, device="cuda")
+        stats = torch.empty(2, dtype=torch.float64, device="cuda")
+        vqmc_shard_apply(self.ctx, sums.contiguous(), scalars.contiguous(), shift, g, stats)
+        return g, stats
 
     # stochastic reconfiguration (FP32 contexts)
     def sr_gram(self, s):

@@ -100,3 +100,110 @@ def test_sharded_global_baseline_gradient_equals_full_batch():
         assert scale > 0
         assert err <= 1e-12 * max(1.0, scale) * 40
         assert dmean <= 1e-12
+
+
+class _OracleShard:
+    """The library's shard calls (vqmc_set_sample_offset, vqmc_shard_sums,
+    vqmc_shard_apply) restated on the FP64 oracle, so that the host protocol
+    of paper_2106_13308_gb300.sharded runs on CPU ranks."""
+
+    def __init__(self, n, h, inst, theta, seed):
+        import oracle
+        self.o = oracle
+        self.n, self.h, self.inst, self.seed = n, h, inst, seed
+        self.theta = np.asarray(theta, np.float64).copy()
+        self.m = np.zeros_like(self.theta)
+        self.v = np.zeros_like(self.theta)
+        self.t = 0
+        self.iter = 0
+        self.b0 = 0
+        self.last_grad = None
+
+    def set_sample_offset(self, b0):
+        self.b0 = int(b0)
+
+    def shard_sums(self, B, shift):
+        o = self.o
+        P = o.theta_to_made(self.theta, self.n, self.h)
+        U = o.uniforms(self.b0 + B, self.n, self.seed, self.iter)[self.b0:]
+        S, _ = o.sample(P, U)
+        E = o.energy(self.inst, S)
+        c1 = E - shift
+        S1 = o.made_to_theta(*o.logprob_grad(P, S, c1))
+        S0 = o.made_to_theta(*o.logprob_grad(P, S, np.ones(B)))
+        return torch.from_numpy(np.concatenate([S1, S0])), torch.tensor([c1.sum(), (c1 * c1).sum(), float(B)],
+                                                                         dtype=torch.float64)
+
+    def shard_apply(self, sums, scal, shift):
+        d = self.theta.size
+        s = sums.numpy()
+        bt = float(scal[2])
+        mm = float(scal[0]) / bt
+        g = (s[:d] - mm * s[d:]) / bt
+        self.t += 1
+        self.o.adam(self.theta, self.m, self.v, g, self.t)
+        self.iter += 1
+        self.last_grad = g
+        return torch.from_numpy(g), torch.tensor([shift + mm, float(scal[1]) / bt - mm * mm], dtype=torch.float64)
+
+
+def _sharded_problem():
+    from paper_2106_13308_gb300 import inputs
+    n, h = 12, 9
+    edges = inputs.erdos_renyi(n, 0.4, 3)
+    inst = inputs.to_csr(n, edges, inputs.int_weights(len(edges), 1, 10, 4))
+    return n, h, inst, inputs.lively_params(n, h, 5)
+
+
+def _sharded_run_worker(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    from paper_2106_13308_gb300.sharded import ShardedRun
+    _init(rank, world, port)
+    n, h, inst, theta = _sharded_problem()
+    model = _OracleShard(n, h, inst, theta, seed=77)
+    run = ShardedRun(model, 20)
+    grads, stats = [], []
+    for _ in range(4):
+        st = run.step()
+        grads.append(model.last_grad.copy())
+        stats.append(st.numpy().copy())
+    out[rank] = (model.theta.copy(), grads, stats, run.batch_total)
+    dist.destroy_process_group()
+
+
+def test_sharded_run_protocol_equals_full_batch_run():
+    """Two gloo ranks of 20 samples each through ShardedRun (sample offsets,
+    one all-reduce of the shard sums, global-baseline gradient, Adam) end
+    with bit-identical parameters, which equal a single-process run of the
+    same protocol on the full batch of 40; the first iteration's gradient
+    equals the oracle's full-batch estimator on the same 40 samples."""
+    import oracle
+    from paper_2106_13308_gb300.sharded import ShardedRun
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_sharded_run_worker, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    th0, g0, st0, bt = res[0]
+    th1, g1, st1, _ = res[1]
+    assert bt == 40
+    assert np.array_equal(th0, th1)
+    n, h, inst, theta = _sharded_problem()
+    full = _OracleShard(n, h, inst, theta, seed=77)
+    run = ShardedRun(full, 40)
+    gf = []
+    for _ in range(4):
+        run.step()
+        gf.append(full.last_grad.copy())
+    scale = max(np.abs(gf[0]).max(), 1e-30)
+    for k in range(4):
+        assert np.max(np.abs(g0[k] - gf[k])) <= 1e-12 * scale * 40, k
+    assert np.max(np.abs(th0 - full.theta)) <= 1e-12
+    # iteration 0 (shift 0) against the oracle's own estimator on the full batch
+    P = oracle.theta_to_made(np.asarray(theta, np.float64), n, h)
+    S, _ = oracle.sample(P, oracle.uniforms(40, n, 77, 0))
+    (dW1, db1, dW2, db2), sto, _ = oracle.vqmc_grad(P, inst, S)
+    ref = oracle.made_to_theta(dW1, db1, dW2, db2)
+    assert np.max(np.abs(g0[0] - ref)) <= 1e-12 * scale * 40
+    assert abs(st0[0][0] - sto[0]) <= 1e-12 * abs(sto[0])
