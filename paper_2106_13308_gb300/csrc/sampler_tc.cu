@@ -46,8 +46,14 @@ using namespace tc;
 
 constexpr int kS = 16;                     // samples per CTA (MMA N)
 constexpr int kRmax = 32;                  // recent units per block
-constexpr int kNStage = 6;                 // weight ring stages
+constexpr int kNStage = 6;                 // weight tiles in the ring
 constexpr int kTileBytes = 128 * 64 * 2;   // one 128 x 64 BF16 tile
+// The ring is consumed in slots of up to two tiles (32 KB): one full-barrier
+// wait and one commit per slot.  The single thread that issues the MMAs pays
+// a fixed cost for every wait and every commit, comparable to the tensor
+// work of an N = 16 tile, so pairing tiles nearly halves the time per tile.
+constexpr int kSlotTiles = 2;
+constexpr int kNSlot = kNStage / kSlotTiles;
 constexpr int kMaxHp = 2048;               // hidden units (padded) in TMEM
 constexpr int kDmax = 128;
 constexpr int kTmemCols = 512;             // A: 16 per 128 units (<= 256), Z at 256
@@ -363,32 +369,40 @@ __global__ void __launch_bounds__(kThreads, 1)
     // Z GEMM of block b+1 over the units complete before block b (W2, block
     // b+1's rows).
     if (lane == 0) {
-      int it = 0;
-      auto load = [&](const CUtensorMap* map, int x, int y) -> bool {
-        const int s = it % kNStage;
-        if (it >= kNStage &&
-            !wait_or_abort(smem_u32(&empty[s]), (uint32_t)((it / kNStage - 1) & 1), abort, g.err, true))
-          return false;
-        const uint32_t bar = smem_u32(&full[s]);
-        mbar_expect_tx(bar, kTileBytes);
-        tma_load_2d(base + kOffRing + s * kTileBytes, map, x, y, bar);
-        ++it;
+      int it = 0;  // slots issued
+      // the tiles [i0, i1) of one phase, two per slot; xy(i, x, y) gives tile i's box
+      auto load_phase = [&](const CUtensorMap* map, int i0, int i1, auto xy) -> bool {
+        for (int i = i0; i < i1; i += kSlotTiles) {
+          const int cnt = min(kSlotTiles, i1 - i);
+          const int s = it % kNSlot;
+          if (it >= kNSlot &&
+              !wait_or_abort(smem_u32(&empty[s]), (uint32_t)((it / kNSlot - 1) & 1), abort, g.err, true))
+            return false;
+          const uint32_t bar = smem_u32(&full[s]);
+          mbar_expect_tx(bar, (uint32_t)(cnt * kTileBytes));
+          for (int j = 0; j < cnt; ++j) {
+            int x, y;
+            xy(i + j, x, y);
+            tma_load_2d(base + kOffRing + (s * kSlotTiles + j) * kTileBytes, map, x, y, bar);
+          }
+          ++it;
+        }
         return true;
       };
       bool ok = true;
       for (int b = 0; b < nblk && ok; ++b) {
         const Blk B = blk_of(b, n, h, D, ntiles, nblk);
-        for (int t = B.crit0; t < B.crit1 && ok; ++t)
-          for (int kk = 0; kk < nkd && ok; ++kk) ok = load(&mapW, (b - 1) * D + 64 * kk, 128 * t);
-        for (int c = B.cor0; c < B.cor1 && ok; ++c) ok = load(&mapV, 64 * c, b * D);
-        for (int t = B.bulk0; t < ntiles && ok; ++t)
-          for (int kk = 0; kk < nkd && ok; ++kk) ok = load(&mapW, (b - 1) * D + 64 * kk, 128 * t);
-        for (int c = 0; c < B.np && ok; ++c) ok = load(&mapV, 64 * c, (b + 1) * D);
+        // update tiles: index q -> unit tile q / nkd, K-chunk q % nkd of block b-1's inputs
+        auto upd = [&](int q, int& x, int& y) { x = (b - 1) * D + 64 * (q % nkd), y = 128 * (q / nkd); };
+        ok = load_phase(&mapW, B.crit0 * nkd, B.crit1 * nkd, upd);
+        if (ok) ok = load_phase(&mapV, B.cor0, B.cor1, [&](int c, int& x, int& y) { x = 64 * c, y = b * D; });
+        if (ok) ok = load_phase(&mapW, B.bulk0 * nkd, ntiles * nkd, upd);
+        if (ok) ok = load_phase(&mapV, 0, B.np, [&](int c, int& x, int& y) { x = 64 * c, y = (b + 1) * D; });
       }
       // no copy may still be landing when the CTA exits (after a failure
       // some loaded tiles are never consumed)
-      for (int p = it > kNStage ? it - kNStage : 0; p < it; ++p)
-        mbar_wait(smem_u32(&full[p % kNStage]), (uint32_t)((p / kNStage) & 1), g.err);
+      for (int p = it > kNSlot ? it - kNSlot : 0; p < it; ++p)
+        mbar_wait(smem_u32(&full[p % kNSlot]), (uint32_t)((p / kNSlot) & 1), g.err);
     }
   } else if (warp == 5) {
     // --------------------------------------------------------- MMA issuer
@@ -398,25 +412,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     // of the update and, once block b-1's recent g1 are in the operand, the Z
     // GEMM of block b+1 into the other Z buffer.
     if (lane == 0) {
-      int it = 0;
+      int it = 0;  // slots consumed
       bool ok = true, any = false;
-      auto take = [&]() -> uint32_t {  // next full ring stage (smem address), or 0
-        const int s = it % kNStage;
-        if (!wait_or_abort(smem_u32(&full[s]), (uint32_t)((it / kNStage) & 1), abort, g.err)) return 0;
-        fence_after();
-        return base + kOffRing + s * kTileBytes;
-      };
-      // one 128 x 64 weight tile against a 16 x 64 operand: 4 MMAs of K = 16
-      auto mma_tile = [&](uint32_t dcol, uint32_t bop, bool acc) -> bool {
-        const uint32_t a = take();
-        if (!a) return false;
-        const uint64_t da = smem_desc_sw128(a), db = smem_desc_sw128(bop);
+      // the tiles [i0, i1) of one phase in the producer's slots; op(i, dcol,
+      // bop, acc) gives tile i's accumulator column, B operand and whether it
+      // accumulates.  Each 128 x 64 weight tile against a 16 x 64 operand is
+      // 4 MMAs of K = 16; one commit releases the slot.
+      auto mma_phase = [&](int i0, int i1, auto op) -> bool {
+        for (int i = i0; i < i1; i += kSlotTiles) {
+          const int cnt = min(kSlotTiles, i1 - i);
+          const int s = it % kNSlot;
+          if (!wait_or_abort(smem_u32(&full[s]), (uint32_t)((it / kNSlot) & 1), abort, g.err)) return false;
+          fence_after();
+          for (int j = 0; j < cnt; ++j) {
+            uint32_t dcol, bop;
+            bool acc;
+            op(i + j, dcol, bop, acc);
+            const uint64_t da = smem_desc_sw128(base + kOffRing + (s * kSlotTiles + j) * kTileBytes);
+            const uint64_t db = smem_desc_sw128(bop);
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          mma_bf16(tmem + dcol, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kIdesc, (acc || k > 0) ? 1u : 0u);
-        mma_commit(smem_u32(&empty[it % kNStage]));
-        ++it;
-        any = true;
+            for (int k = 0; k < 4; ++k)
+              mma_bf16(tmem + dcol, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kIdesc,
+                       (acc || k > 0) ? 1u : 0u);
+          }
+          mma_commit(smem_u32(&empty[s]));
+          ++it;
+          any = true;
+        }
         return true;
       };
       for (int b = 0; b < nblk; ++b) {
@@ -426,20 +448,27 @@ __global__ void __launch_bounds__(kThreads, 1)
           ok = wait_or_abort(smem_u32(ready), (uint32_t)((b - 1) & 1), abort, g.err, true);
           fence_after();
         }
-        for (int t = B.crit0; t < B.crit1 && ok; ++t)
-          for (int kk = 0; kk < nkd && ok; ++kk) ok = mma_tile((uint32_t)(16 * t), s_prev + kk * 2048, true);
+        // update tiles: index q -> accumulator of unit tile q / nkd, K-chunk q % nkd of block b-1's spins
+        auto upd = [&](int q, uint32_t& dcol, uint32_t& bop, bool& acc) {
+          dcol = (uint32_t)(16 * (q / nkd)), bop = s_prev + (q % nkd) * 2048, acc = true;
+        };
+        if (ok) ok = mma_phase(B.crit0 * nkd, B.crit1 * nkd, upd);
         const uint32_t zcol = kZCol + 16 * (b & 1);
-        for (int c = B.cor0; c < B.cor1 && ok; ++c)
-          ok = mma_tile(zcol, base + kOffHr + (c - B.cor0) * 2048, B.zinit || c > B.cor0);
+        if (ok)
+          ok = mma_phase(B.cor0, B.cor1, [&](int c, uint32_t& dcol, uint32_t& bop, bool& acc) {
+            dcol = zcol, bop = base + kOffHr + (c - B.cor0) * 2048, acc = B.zinit || c > B.cor0;
+          });
         if (ok && any) mma_commit(smem_u32(zfull));  // also covers the previous block's work
         else mbar_arrive(smem_u32(zfull));
-        for (int t = B.bulk0; t < ntiles && ok; ++t)
-          for (int kk = 0; kk < nkd && ok; ++kk) ok = mma_tile((uint32_t)(16 * t), s_prev + kk * 2048, true);
+        if (ok) ok = mma_phase(B.bulk0 * nkd, ntiles * nkd, upd);
         if (B.np > 0 && ok) {
           ok = wait_or_abort(smem_u32(merged), (uint32_t)(b & 1), abort, g.err, true);
           fence_after();
           const uint32_t zn = kZCol + 16 * ((b + 1) & 1);
-          for (int c = 0; c < B.np && ok; ++c) ok = mma_tile(zn, base + kOffH + c * 2048, c > 0);
+          if (ok)
+            ok = mma_phase(0, B.np, [&](int c, uint32_t& dcol, uint32_t& bop, bool& acc) {
+              dcol = zn, bop = base + kOffH + c * 2048, acc = c > 0;
+            });
         }
       }
       // every MMA has completed before tensor memory is released
