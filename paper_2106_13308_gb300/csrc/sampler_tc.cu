@@ -78,10 +78,10 @@ constexpr int kOffLG = kOffZ + kDrows * kZld * 4;              // logit(u) [2][k
 constexpr int kOffP = kOffLG + 2 * kDrows * kS * 4;            // recent pre-activations at block start [32][16]
 constexpr int kOffWr = kOffP + kRmax * kS * 4;                 // W1 of recent units [kDrows][kLdW] bf16
 constexpr int kOffVr = kOffWr + kDrows * kLdW * 2;             // W2 of recent units [kDrows][kLdW] bf16
-constexpr int kOffPS = kOffVr + kDrows * kLdW * 2;             // solver: current pre-activations [16][kLdP]
-constexpr int kOffHF = kOffPS + kS * kLdP * 4;                 // solver: frozen g1 [16][kLdP]
+constexpr int kOffPS = kOffVr + kDrows * kLdW * 2;             // solver: g1 of the recent units [16][kLdP]
+constexpr int kOffHF = kOffPS + kS * kLdP * 4;                 // (unused)
 constexpr int kOffSB = kOffHF + kS * kLdP * 4;                 // drawn spins, bit e%32 of word [2][16][e/32]
-constexpr int kOffCU = kOffSB + 2 * kS * (kDmax / 32) * 4;     // unit completing at step e-2, [D+5] int
+constexpr int kOffCU = kOffSB + 2 * kS * (kDmax / 32) * 4;     // completion step of each recent unit, [kRmax] int
 constexpr int kOffBar = kOffCU + (kDmax + 8) * 4;              // mbarriers + slots
 constexpr int kSmemBytes = 1024 + kOffBar + 128;
 static_assert(kSmemBytes <= 232448, "shared memory budget");
@@ -137,125 +137,143 @@ __device__ __forceinline__ float g1f(float a) {
   else return 1.0f / (1.0f + expf(-a));
 }
 
-// The sequential part of a block: lanes 4s..4s+3 of warps 2-3 draw the spins
-// of sample s; lane 4s+sub owns recent units 8 sub .. 8 sub + 7 (their
-// pre-activations).  With h < n at most one unit completes per step (cu[e]:
-// the unit whose last input is the spin of step e), and
-//     z_e = (Z_e + b2) + sum_{u done by step e-2} W2_eu g1_u    (off the chain)
-//                      + W2_eu1 g1(a_u1 + W1_u1,e-1 s_{e-1})     (u1 = cu[e-1])
-// so the dependence of step e on step e-1 is one FMA, the activation, the
-// BF16 rounding, one FMA and the compare.  The rest of z_{e+2} is assembled
-// two steps ahead: units frozen into hf (done by step e-3; a 4-lane shuffle
-// reduction) plus one explicit term for each later unit.  Every shared-memory
-// operand of step e+1 is loaded during step e, after the lanes have published
-// their pre-activations (for the owner lookup of the next completing unit)
-// and the frozen g1 of the unit done two steps before.  W2_eu is zero for
-// units not yet complete and W1_uj is zero for inputs after a unit's last one,
-// so no masks are needed.
+// The sequential part of a block: the draws of its D steps, carried by
+// lanes 4s..4s+3 of warps 2-3 for sample s.  With sorted degrees at most
+// one hidden unit completes per step (h < n), and the logit of step e
+// depends on the earlier spins only through the units completed before e:
+//     z_e = (Z_e + b2) + sum_{recent r: t_r < e} W2_{e,r} g1_r,
+// t_r the step whose spin is recent unit r's last input.  So the steps
+// between two completions, (t_{r-1}, t_r], are conditionally independent
+// given g1_0 .. g1_{r-1}: they form one segment, drawn in parallel.  Lane q
+// draws the steps e = q (mod 4) and keeps, for all 32 recent units, its own
+// partial pre-activation sum over the spins it drew (lane 0 also holds the
+// value at the start of the block).  When segment r ends, unit r's four
+// partials are added with two shuffles, and g1_r = bf16(act(a_r)) enters
+// the logits of the later segments.  The chain from one completion to the
+// next is: the shuffle reduction, the activation and the rounding, one FMA
+// with W2_{e,r} (the rest of the lane's next logit is summed before the
+// reduction), the compare, and the lane's partial sum of unit r+1.  W2_{e,r}
+// is zero for units not complete before step e and W1 for inputs after a
+// unit's last one, so no masks are applied; g1 is zero (HH) until a unit
+// completes.  HH holds each sample's recent g1 in shared memory (written by
+// all four lanes with the same value).
 template <int ACT, bool LP>
 __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf16* Wr, const float* Zs,
-                                      const float* LG, const int* CU, uint32_t* SB, float* PreS, float* HfS,
-                                      unsigned char* Hr, int s_me, int sub, int klo, int R, int steps, float& lp) {
-  float pre[8];
+                                      const float* LG, const int* TC, uint32_t* SB, float* HH, unsigned char* Hr,
+                                      int s_me, int q, int klo, int R, int steps, float& lp) {
+  float* hh = HH + s_me * kLdP;
+  float P[kRmax];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) pre[j] = Pr[(8 * sub + j) * kS + s_me];
-  float* my_pre = PreS + s_me * kLdP + 8 * sub;
-  const float* my_hf = HfS + s_me * kLdP + 8 * sub;
-  const float* pre_row = PreS + s_me * kLdP;
-  float* hf_row = HfS + s_me * kLdP;
-  reinterpret_cast<float4*>(my_pre)[0] = make_float4(pre[0], pre[1], pre[2], pre[3]);
-  reinterpret_cast<float4*>(my_pre)[1] = make_float4(pre[4], pre[5], pre[6], pre[7]);
-  reinterpret_cast<float4*>(hf_row + 8 * sub)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-  reinterpret_cast<float4*>(hf_row + 8 * sub)[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = 0; k < kRmax; ++k) P[k] = q == 0 ? Pr[k * kS + s_me] : 0.0f;
+  reinterpret_cast<float4*>(hh)[2 * q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  reinterpret_cast<float4*>(hh)[2 * q + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncwarp();
-  auto wt = [&](int e, int u) { return __bfloat162float(Wr[e * kLdW + u]); };
-  auto vt = [&](int e, int u) { return __bfloat162float(Vr[e * kLdW + u]); };
-  // chain state of step e (cu[-1] = cu[-2] = none)
-  float sv = 0.0f, pc_old = 0.0f, Wc = 0.0f, Vc = 0.0f, h2 = 0.0f;
-  float zbA = Zs[s_me], lg = LG[s_me];
-  float Qp = Zs[kZld + s_me], app = 0.0f;  // z_{e+1} minus the units of steps >= e-1: Qp + app
-  // operands of step e, loaded one step ahead
-  int u0 = CU[2], u1 = kRmax, u2 = kRmax, u0n = CU[3];
-  uint4 wrow = *reinterpret_cast<const uint4*>(Wr + 8 * sub);
-  uint4 vrow = *reinterpret_cast<const uint4*>(Vr + 2 * kLdW + 8 * sub);
-  float4 ha = make_float4(0.f, 0.f, 0.f, 0.f), hb = ha;
-  float Wcn = wt(0, u0), Vcn = vt(1, u0), v1 = 0.0f, v2 = 0.0f, w2 = 0.0f;
-  float zs2 = Zs[2 * kZld + s_me], lgn = LG[kS + s_me], pc_oldn = pre_row[u0];
-  uint32_t bits = 0;
-#pragma unroll 2
-  for (int e = 0; e < steps; ++e) {
-    // ---- the chain of step e
-    const float pc = fmaf(Wc, sv, pc_old);
-    const float h1 = bf16r(g1f<ACT>(pc));  // g1 of cu[e-1] (unused when there is none: Vc = 0)
-    const float z = fmaf(Vc, h1, zbA);
-    const bool up = z > lg;  // u < sigma(z)
-    const float svn = up ? 1.0f : -1.0f;
-    // ---- units frozen by step e-3, at step e+2 (consumed at step e+1)
-    float a0 = 0.0f, a1 = 0.0f;
-    {
-      const uint32_t vw[4] = {vrow.x, vrow.y, vrow.z, vrow.w};
-      a0 = bf_lo(vw[0]) * ha.x;
-      a1 = bf_hi(vw[0]) * ha.y;
-      a0 = fmaf(bf_lo(vw[1]), ha.z, a0);
-      a1 = fmaf(bf_hi(vw[1]), ha.w, a1);
-      a0 = fmaf(bf_lo(vw[2]), hb.x, a0);
-      a1 = fmaf(bf_hi(vw[2]), hb.y, a1);
-      a0 = fmaf(bf_lo(vw[3]), hb.z, a0);
-      a1 = fmaf(bf_hi(vw[3]), hb.w, a1);
-    }
-    float ap = a0 + a1;
-    ap += __shfl_xor_sync(0xffffffffu, ap, 1);
-    ap += __shfl_xor_sync(0xffffffffu, ap, 2);
-    // ---- owned pre-activations take s_e
-    {
-      const uint32_t wv[4] = {wrow.x, wrow.y, wrow.z, wrow.w};
+  uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;  // this lane's drawn spins: bit e % 32 of word e / 32
+  // Z_e + b2 + the terms of the recent units completed so far (hh)
+  auto zdot = [&](int e) -> float {
+    const uint4* vr = reinterpret_cast<const uint4*>(Vr + e * kLdW);
+    const float4* hv = reinterpret_cast<const float4*>(hh);
+    float a0 = Zs[e * kZld + s_me], a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        pre[2 * q] = fmaf(bf_lo(wv[q]), svn, pre[2 * q]);
-        pre[2 * q + 1] = fmaf(bf_hi(wv[q]), svn, pre[2 * q + 1]);
-      }
+    for (int c = 0; c < 4; ++c) {
+      const uint4 v = vr[c];
+      const float4 x = hv[2 * c], y = hv[2 * c + 1];
+      a0 = fmaf(bf_lo(v.x), x.x, a0);
+      a1 = fmaf(bf_hi(v.x), x.y, a1);
+      a2 = fmaf(bf_lo(v.y), x.z, a2);
+      a3 = fmaf(bf_hi(v.y), x.w, a3);
+      a0 = fmaf(bf_lo(v.z), y.x, a0);
+      a1 = fmaf(bf_hi(v.z), y.y, a1);
+      a2 = fmaf(bf_lo(v.w), y.z, a2);
+      a3 = fmaf(bf_hi(v.w), y.w, a3);
     }
-    // ---- z_{e+1} without its chain term; z_{e+2} without the units of steps >= e
-    zbA = fmaf(v1, h1, Qp + app);
-    Qp = fmaf(v2, h1, fmaf(w2, h2, zs2));
-    app = ap;
-    const uint32_t nb = bits | ((up ? 1u : 0u) << (e & 31));
-    SB[s_me * (kDmax / 32) + (e >> 5)] = nb;  // the 4 lanes of the sample store the same word
-    bits = (e & 31) == 31 ? 0u : nb;
+    return (a0 + a1) + (a2 + a3);
+  };
+  // draw of step e from its logit, and the spin into this lane's partial sums
+  auto draw = [&](int e, float z) {
+    const bool up = z > LG[e * kS + s_me];  // u < sigma(z)
+    const uint32_t m = up ? 1u << (e & 31) : 0u;
+    const int wd = e >> 5;
+    w0 |= wd == 0 ? m : 0u;
+    w1 |= wd == 1 ? m : 0u;
+    w2 |= wd == 2 ? m : 0u;
+    w3 |= wd == 3 ? m : 0u;
     if constexpr (LP) lp += log_sigmoid(up ? z : -z);
-    // ---- publish, then load the operands of step e+1
-    __syncwarp();                 // the lanes have read this step's tables
-    hf_row[u2] = h2;              // freeze g1 of cu[e-2] (column kRmax when there is none)
-    reinterpret_cast<float4*>(my_pre)[0] = make_float4(pre[0], pre[1], pre[2], pre[3]);
-    reinterpret_cast<float4*>(my_pre)[1] = make_float4(pre[4], pre[5], pre[6], pre[7]);
-    __syncwarp();
-    const int u0nn = CU[e + 4];
-    wrow = *reinterpret_cast<const uint4*>(Wr + (e + 1) * kLdW + 8 * sub);
-    vrow = *reinterpret_cast<const uint4*>(Vr + (e + 3) * kLdW + 8 * sub);
-    ha = reinterpret_cast<const float4*>(my_hf)[0];
-    hb = reinterpret_cast<const float4*>(my_hf)[1];
-    const float Wcnn = wt(e + 1, u0n), Vcnn = vt(e + 2, u0n);
-    v1 = vt(e + 2, u0);
-    v2 = vt(e + 3, u0);
-    w2 = vt(e + 3, u1);
-    zs2 = Zs[(e + 3) * kZld + s_me];
-    const float lgnn = LG[(e + 2) * kS + s_me];
-    const float pc_oldnn = pre_row[u0n];
-    h2 = h1, sv = svn, pc_old = pc_oldn, Wc = Wcn, Vc = Vcn, lg = lgn;
-    pc_oldn = pc_oldnn, Wcn = Wcnn, Vcn = Vcnn, lgn = lgnn;
-    u2 = u1, u1 = u0, u0 = u0n, u0n = u0nn;
+    const float sv = up ? 1.0f : -1.0f;
+    const uint4* wr = reinterpret_cast<const uint4*>(Wr + e * kLdW);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint4 w = wr[c];
+      P[8 * c + 0] = fmaf(bf_lo(w.x), sv, P[8 * c + 0]);
+      P[8 * c + 1] = fmaf(bf_hi(w.x), sv, P[8 * c + 1]);
+      P[8 * c + 2] = fmaf(bf_lo(w.y), sv, P[8 * c + 2]);
+      P[8 * c + 3] = fmaf(bf_hi(w.y), sv, P[8 * c + 3]);
+      P[8 * c + 4] = fmaf(bf_lo(w.z), sv, P[8 * c + 4]);
+      P[8 * c + 5] = fmaf(bf_hi(w.z), sv, P[8 * c + 5]);
+      P[8 * c + 6] = fmaf(bf_lo(w.w), sv, P[8 * c + 6]);
+      P[8 * c + 7] = fmaf(bf_hi(w.w), sv, P[8 * c + 7]);
+    }
+  };
+  float g_last = 0.0f;       // g1 of the unit that completed last
+  bool pf = false;           // this lane's first step of the segment was prepared
+  float zp = 0.0f, vn = 0.0f;  // ... its logit without the last unit, and that unit's weight on it
+  int lo = 0;
+  for (int r = 0; r <= R; ++r) {  // segment r: steps [lo, hi], units 0 .. r-1 complete
+    const int hi = r < R ? TC[r] : steps - 1;
+    if (r > 0) hh[r - 1] = g_last;
+    int e = lo + ((q - lo) & 3);
+    if (e <= hi) {
+      draw(e, pf ? fmaf(vn, g_last, zp) : zdot(e));
+      for (e += 4; e <= hi; e += 4) draw(e, zdot(e));
+    }
+    if (r == R) break;
+    // the next segment's first step of this lane, without unit r
+    const int nlo = hi + 1, nhi = r + 1 < R ? TC[r + 1] : steps - 1;
+    const int en = nlo + ((q - nlo) & 3);
+    pf = en <= nhi;
+    if (pf) {
+      zp = zdot(en);
+      vn = __bfloat162float(Vr[en * kLdW + r]);
+    }
+    // unit r completes: its partial sums of the four lanes (a binary select of P[r])
+    float x;
+    {
+      float l1[16], l2[8], l3[4], l4[2];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) l1[k] = (r & 1) ? P[2 * k + 1] : P[2 * k];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) l2[k] = (r & 2) ? l1[2 * k + 1] : l1[2 * k];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) l3[k] = (r & 4) ? l2[2 * k + 1] : l2[2 * k];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) l4[k] = (r & 8) ? l3[2 * k + 1] : l3[2 * k];
+      x = (r & 16) ? l4[1] : l4[0];
+    }
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    g_last = bf16r(g1f<ACT>(x));
+    lo = nlo;
   }
+  // the sample's spins: the four lanes' words combined; lane q stores word q
+#pragma unroll
+  for (int d = 1; d <= 2; d <<= 1) {
+    w0 |= __shfl_xor_sync(0xffffffffu, w0, d);
+    w1 |= __shfl_xor_sync(0xffffffffu, w1, d);
+    w2 |= __shfl_xor_sync(0xffffffffu, w2, d);
+    w3 |= __shfl_xor_sync(0xffffffffu, w3, d);
+  }
+  if (q < kDmax / 32) SB[s_me * (kDmax / 32) + q] = q == 0 ? w0 : q == 1 ? w1 : q == 2 ? w2 : w3;
   // every recent unit is complete: its g1 goes to the staging operand Hr
   // (2 chunks of 64 units from chunk klo / 64), once warps 0-1 have moved
   // the previous block's recent g1 out of it
   asm volatile("bar.sync 2, 128;" ::: "memory");
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int r = 8 * sub + j;
+  for (int j = 0; j < kRmax / 4; ++j) {
+    const int r = q + 4 * j;
     if (r < R) {
       const int k = klo + r;
       *reinterpret_cast<bf16*>(Hr + ((k >> 6) - (klo >> 6)) * 2048 + sw128_offset(s_me, k & 63)) =
-          __float2bfloat16_rn(g1f<ACT>(pre[j]));
+          __float2bfloat16_rn(hh[r]);
     }
   }
 }
@@ -303,7 +321,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   bf16* Wr = reinterpret_cast<bf16*>(sm + kOffWr);
   bf16* Vr = reinterpret_cast<bf16*>(sm + kOffVr);
   float* PreS = reinterpret_cast<float*>(sm + kOffPS);
-  float* HfS = reinterpret_cast<float*>(sm + kOffHF);
   uint32_t* SB = reinterpret_cast<uint32_t*>(sm + kOffSB);
   int* CU = reinterpret_cast<int*>(sm + kOffCU);
   const unsigned long long it_all = g.it_dev ? *g.it_dev : ((unsigned long long)g.it1 << 32 | g.it0);
@@ -614,15 +631,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int steps = min(D, n - b * D);
       // (a) the recent units' completion steps (their weights are in Vr / Wr)
       for (int q = tid; q < (kRmax - R) * kS; q += 128) Pr[R * kS + q] = 0.0f;
-      for (int e = tid; e < D + 5; e += 128) {  // CU[e] = unit completing at step e - 2
-        const int x = b * D + e - 2;             // its degree would be x + 1
-        int u = kRmax;
-        if (e >= 2 && e - 2 < steps) {
-          const int k = count_deg_le(x + 1, n, h);
-          if (k > count_deg_le(x, n, h)) u = k - 1 - klo;
-        }
-        CU[e] = u;
-      }
+      // TC[r] = the block step whose spin is recent unit r's last input
+      for (int r = tid; r < kRmax; r += 128) CU[r] = r < R ? degree(klo + r, n, h) - 1 - b * D : D;
       // (b) Z and the recent pre-activations from tensor memory
       wait_or_abort(smem_u32(zfull), (uint32_t)(b & 1), abort, g.err);
       __syncwarp();
@@ -664,11 +674,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float* L = LG + (b & 1) * kDrows * kS;
         uint32_t* sb = SB + (b & 1) * kS * (kDmax / 32);
         if (g.logp) {
-          if (relu) solve<VQMC_ACT_RELU, true>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, HfS, Hr, s_me, sub, klo, R, steps, lp);
-          else solve<VQMC_ACT_SIGMOID, true>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, HfS, Hr, s_me, sub, klo, R, steps, lp);
+          if (relu) solve<VQMC_ACT_RELU, true>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, Hr, s_me, sub, klo, R, steps, lp);
+          else solve<VQMC_ACT_SIGMOID, true>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, Hr, s_me, sub, klo, R, steps, lp);
         } else {
-          if (relu) solve<VQMC_ACT_RELU, false>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, HfS, Hr, s_me, sub, klo, R, steps, lp);
-          else solve<VQMC_ACT_SIGMOID, false>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, HfS, Hr, s_me, sub, klo, R, steps, lp);
+          if (relu) solve<VQMC_ACT_RELU, false>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, Hr, s_me, sub, klo, R, steps, lp);
+          else solve<VQMC_ACT_SIGMOID, false>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, Hr, s_me, sub, klo, R, steps, lp);
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
         // (d) 8 spins of one sample per 16-byte store (+1 = 0x3F80, -1 = 0xBF80)
@@ -712,6 +722,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
     write_spins(nblk - 1, tid, 128);
+    if (warp >= 2) {  // the four lanes' partial sums of log pi
+      lp += __shfl_xor_sync(0xffffffffu, lp, 1);
+      lp += __shfl_xor_sync(0xffffffffu, lp, 2);
+    }
     if (warp >= 2 && sub == 0 && g.logp && b0 + s_me < g.B && !*abort) g.logp[b0 + s_me] = lp;
   }
 
