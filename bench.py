@@ -23,12 +23,21 @@ under "sr": its iteration adds the B x B Gram matrix of the per-sample score
 vectors, a Cholesky solve and a second adjoint pass.  --sr-only runs this arm
 alone (the command the SR profiles were taken with).
 
+Two more workloads of the benchmark family are timed the same way (BF16,
+Adam) and reported under "other_workloads": the dense Sherrington-Kirkpatrick
+spin glass (n = 2000, h = 2000, B = 8192; the local energy is a tcgen05 GEMM
+with a BF16 hi/lo split of J, with its roofline) and Max-Cut on a random
+3-regular graph (n = h = 1000, B = 4096).  "bf16_vs_fp32" states the BF16
+path's distance from the plain FP32 path at the benchmark workload, and
+"equal_energy" compares the two precisions' final energies after 300 Adam
+iterations over 5 seeds.
+
 A fourth, many independent instances trained together: 64 Max-Cut instances of
-uneven size (n ~ U{100..5000}, G(n, 6/(n-1)), weights +-1, 512 samples each,
-hidden units min(n, 2048): the samplers hold at most 2048), BF16, stepped as
-one CUDA graph launch per batched iteration under the schedule the library's
-autotuner picked; reported under "batched" beside the same batch stepped call
-by call.
+uneven size (n ~ U{100..5000}, G(n, 6/(n-1)), weights +-1, hidden units h = n,
+512 samples each), BF16, stepped as one CUDA graph launch per batched
+iteration under the schedule and sampler layouts the library's autotuner
+picked; reported under "batched" beside the same batch stepped call by call,
+with the lower bound of the longest member's iteration alone.
 
 --impl reference times the FP64 CPU oracle on the host cores instead (a
 bounded sub-batch per step, scaled linearly to the full batch).
@@ -86,6 +95,22 @@ def _bf16_peak():
         return float(p["bf16_tflops_sustained"]), "measured: bf16_tflops_sustained (cuBLAS bf16 GEMM, seconds-long loop)"
     except (OSError, KeyError, ValueError):
         return 1700.0, "fallback: sustained bf16 of an earlier GB300 measurement"
+
+
+def _fp32_peak():
+    """FP32 FMA peak of this GPU from its SM count (read at run time), 128 FP32
+    lanes per SM and 2 flop per FMA, at the maximum SM clock (the driver's
+    measured record, else the GB300's 2070 MHz); there is no measured FP32
+    peak."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz, src = 2070.0, "GB300 maximum SM clock"
+    try:
+        mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+        src = "sm_max_mhz of MEASURED_PEAKS.json"
+    except (OSError, KeyError, ValueError):
+        pass
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, f"derived: {sms} SMs (read at run time) x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz ({src})"
 
 
 def _workload(name):
@@ -261,7 +286,7 @@ def _sr_arm(K, W, dist_on, world):
     torch.cuda.synchronize()
     gram_ms = g0.elapsed_time(g1) / K
     gflop = 5.0 * (n + h) * B * (B + 1) / 2
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    fp32_peak, _, fp32_src = _fp32_peak()
     ach = gflop / (gram_ms / 1000.0) / 1e12
     out = {"workload": f"{TIM_WORKLOAD} in FP32: transverse-field Ising, n={n}, MADE h={h} {cfg['act']}, "
                        f"batch {B}; SGD+SR with lambda={lam}, lr={lr} (Sec. 5.1)",
@@ -270,11 +295,55 @@ def _sr_arm(K, W, dist_on, world):
            "gram_call_ms": gram_ms,
            "roofline_gram": {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                              "frac": ach / fp32_peak,
-                             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                             "peak_source": fp32_src,
                              "algorithmic": f"5*(n+h)*B*(B+1)/2 = {gflop:.3e} flop per Gram matrix; timed over "
                                             "the whole vqmc_sr_gram call (operand GEMMs included), so a lower "
                                             "bound on the kernel's own rate"},
            "device_error_flags": m.check()}
+    del m
+    return out
+
+
+def _config_arm(name, K, W, dist_on, world):
+    """The BF16 iteration (vqmc_step) at another workload of the benchmark
+    family, with the library's per-part times: the dense Sherrington-
+    Kirkpatrick spin glass (sk2000: n = 2000, h = 2000, B = 8192, J ~ N(0, 1/n)
+    dense FP32, local energy as a tcgen05 GEMM S J with a BF16 hi/lo split of
+    J) or the random 3-regular Max-Cut graph (maxcut_3reg1000: n = h = 1000,
+    B = 4096, weights +-1; h >= n, so the CUDA-core sampler)."""
+    import torch
+    cfg, inst = _workload(name)
+    B, n, h = cfg["B"], cfg["n"], cfg["h"]
+    m = _make(cfg, inst, "bf16")
+    ms, parts, steps, launches = _timed_steps(m, B, K, W, dist_on)
+    ms, val = _replica_rate(ms, K, world, "cuda")
+    part = {k: v / max(steps, 1) for k, v in parts.items()}
+    peak, peak_src = _bf16_peak()
+    out = {"value": val, "unit": UNIT, "ms_per_step": ms / K, "samples_per_s": val * B, "steps": K,
+           "part_ms": part, "gpu_launches": launches, "device_error_flags": m.check()}
+    if inst["kind"] == "dense":
+        out["workload"] = (f"{name}: Sherrington-Kirkpatrick spin glass, n={n}, dense J_ij ~ N(0, 1/n) float32, h = 0; "
+                           f"MADE h={h} {cfg['act']}; batch {B}; BF16, Adam")
+        # the energy part is the tcgen05 GEMM S J (two BF16 passes, J's high part and remainder) plus a
+        # row reduction kernel
+        eflop = 2 * 2.0 * B * n * n
+        ach = eflop / (part["energy"] / 1000.0) / 1e12
+        out["roofline_energy"] = {"bound": "tensor", "kernel": "gemm_tc_kernel<kOpEloc>", "achieved": ach,
+                                  "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "peak_source": peak_src,
+                                  "algorithmic": f"2 passes x 2*B*n^2 = {eflop:.3e} flop per energy evaluation "
+                                                 "over the step's energy part, which also holds the spin-operand and "
+                                                 "row-reduction kernels: a lower bound on the GEMM's own rate"}
+    else:
+        out["workload"] = (f"{name}: Max-Cut on a random 3-regular graph, n={n}, weights +-1 (int32 CSR); MADE h={h} "
+                           f"{cfg['act']}; batch {B}; BF16, Adam (h >= n: CUDA-core sampler)")
+    sflop = 2.0 * h * n * B
+    fp32_peak, _, fp32_src = _fp32_peak()
+    sach = sflop / (part["sample"] / 1000.0) / 1e12
+    out["roofline_sampler"] = {"bound": "alu" if n <= h else "tensor", "achieved": sach,
+                               "peak": fp32_peak if n <= h else peak, "unit": "TFLOP/s",
+                               "frac": sach / (fp32_peak if n <= h else peak),
+                               "peak_source": fp32_src if n <= h else peak_src,
+                               "algorithmic": f"2*h*n*B = {sflop:.3e} flop per launch"}
     del m
     return out
 
@@ -286,7 +355,7 @@ def _batched_arm(K, W, dist_on, world):
     from paper_2106_13308_gb300 import inputs
     from paper_2106_13308_gb300.vqmc import VQMCBatch
     cfgs = inputs.batched_configs()
-    probs = [dict(n=c["n"], h=min(c["h"], 2048), max_batch=c["B"], instance=inputs.make_instance(c), act=c["act"],
+    probs = [dict(n=c["n"], h=c["h"], max_batch=c["B"], instance=inputs.make_instance(c), act=c["act"],
                   precision="bf16", seed=c["graph_seed"]) for c in cfgs]
     Bs = [p["max_batch"] for p in probs]
     batch = VQMCBatch(probs)
@@ -326,13 +395,19 @@ def _batched_arm(K, W, dist_on, world):
         graph_ms_total = g0.elapsed_time(g1)
     flags = [m.check() for m in batch.members]
     graph_ms, val = _replica_rate(graph_ms_total, K, world, "cuda")
+    used, mstream, samplers, alone = batch.schedule()
     ns = [c["n"] for c in cfgs]
     out = {"workload": f"{len(cfgs)} Max-Cut instances, n ~ U{{100..5000}} (min {min(ns)}, max {max(ns)}), "
-                       "G(n, 6/(n-1)), weights +-1, MADE h = min(n, 2048) relu, 512 samples each, BF16, Adam",
+                       "G(n, 6/(n-1)), weights +-1, MADE h = n relu, 512 samples each, BF16, Adam",
            "value": val, "unit": "batched it/s", "ms_per_step": graph_ms / K,
            "samples_per_s": val * sum(Bs), "steps": K,
            "eager_ms_per_step": eager_ms, "autotuned_streams": streams, "autotune_ms_per_step": tuned_ms,
-           "autotune_wall_s": tune_s, "device_error_flags": int(any(flags))}
+           "autotune_wall_s": tune_s,
+           "autotuned_samplers": {k: samplers.count(k) for k in sorted(set(samplers))},
+           # each member's kernels run in order, so the longest member alone bounds a batched iteration
+           "bound_ms_longest_member_alone": max(alone), "serial_ms_members_one_after_another": sum(alone),
+           "fraction_of_bound": max(alone) / (graph_ms / K),
+           "device_error_flags": int(any(flags))}
     batch.close()
     return out
 
@@ -487,6 +562,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the many-instances arm")
     ap.add_argument("--batched-only", action="store_true", help="run only the many-instances arm")
     ap.add_argument("--no-quant", action="store_true", help="skip the BF16-vs-FP32 quantisation figures")
+    ap.add_argument("--no-other", action="store_true", help="skip the sk2000 and maxcut_3reg1000 workloads")
     ap.add_argument("--no-equal-energy", action="store_true",
                     help="skip the 5-seed x 300-iteration equal-energy comparison")
     args = ap.parse_args()
@@ -625,6 +701,13 @@ def main():
                "device_error_flags": mt.check()}
         del mt
 
+    others = None
+    if not args.no_other:
+        others = {}
+        for nm in ("sk2000", "maxcut_3reg1000"):
+            torch.cuda.empty_cache()
+            others[nm] = _config_arm(nm, max(3, K // 2), W, dist_on, world)
+
     sr = None
     if not args.no_sr:
         torch.cuda.empty_cache()
@@ -648,7 +731,8 @@ def main():
                 # exact samples per second of the sampler alone (uniforms are drawn inside it)
                 "sampler_samples_per_s": world * B / (sample_ms / 1000.0),
                 "part_ms": part_ms, "fp32": fp32, "bf16_vs_fp32": quant, "equal_energy": equal,
-                "tim": tim, "sr": sr, "batched": batched,
+                "tim": tim, "sr": sr, "batched": batched, "other_workloads": others,
+                "num_sms": _fp32_peak()[1],
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clk, "device_error_flags": flags}

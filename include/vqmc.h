@@ -75,10 +75,16 @@ enum { VQMC_ACT_RELU = 0, VQMC_ACT_SIGMOID = 1 };
  * gradients are FP32 in both modes; batch statistics are FP64. */
 enum { VQMC_PREC_FP32 = 0, VQMC_PREC_BF16 = 1 };
 
-/* Sampler implementation (vqmc_config.sampler).  Both draw the same exact
+/* Sampler implementation (vqmc_config.sampler).  All draw the same exact
  * samples of the model (Algorithm 1) from the same uniforms.
  *   AUTO: TENSOR_CORE where it applies, else CUDA_CORE.
- *   CUDA_CORE: one step at a time, FP32 FMAs on the CUDA cores; any model.
+ *   CUDA_CORE: one step at a time, FP32 FMAs on the CUDA cores; any model
+ *     with h <= 5120 (BF16 weights) or h <= 2816 (FP32 weights).  Up to
+ *     h = 2048 a CTA carries 16 samples; beyond, 4.
+ *   CUDA_CORE_WIDE: the CUDA-core sampler with the layout it uses beyond
+ *     h = 2048 (groups of four warps split the hidden units, 4 samples per
+ *     CTA) at any h: four times the CTAs, fewer registers per sample; the
+ *     batch autotuner chooses between the two per member.
  *   TENSOR_CORE: blocks of 64 or 128 steps whose bulk work (the logits from
  *     hidden units completed before the block, and the update of hidden
  *     units by the block's spins) runs as tcgen05 GEMMs, with a sequential
@@ -86,7 +92,7 @@ enum { VQMC_PREC_FP32 = 0, VQMC_PREC_BF16 = 1 };
  *     only, h <= 2048, and at most 32 hidden units completing within 64
  *     consecutive steps (h up to about n/2); vqmc_create returns UNSUPPORTED
  *     when it is requested for any other model. */
-enum { VQMC_SAMPLER_AUTO = 0, VQMC_SAMPLER_CUDA_CORE = 1, VQMC_SAMPLER_TENSOR_CORE = 2 };
+enum { VQMC_SAMPLER_AUTO = 0, VQMC_SAMPLER_CUDA_CORE = 1, VQMC_SAMPLER_TENSOR_CORE = 2, VQMC_SAMPLER_CUDA_CORE_WIDE = 3 };
 
 /* Hamiltonian storage. */
 enum {
@@ -400,18 +406,31 @@ vqmc_status vqmc_batch_graph_capture(vqmc_batch* batch, const int32_t* B, int32_
  * counters advance by their number.  h_out: NULL or `count` records. */
 vqmc_status vqmc_batch_graph_launch(vqmc_batch* batch, vqmc_stream stream, vqmc_step_stats* h_out);
 
-/* Autotuner of the batch's schedule: measures one iteration of each member
- * alone, then times one captured batched iteration (graph replays) under
- * each candidate schedule -- 1, 2, 4, ... up to the batch's internal streams,
- * with members assigned round-robin in index order or longest first onto
- * the least-loaded stream -- and keeps the fastest schedule, with its
- * captured graph (one iteration, for vqmc_batch_graph_launch).  The
- * iterations it times are ordinary iterations of every member: each member
- * advances by 2 + 4 x (number of candidates) iterations.  streams_out and
- * ms_out (NULL allowed) receive the chosen number of streams and its device
- * time per batched iteration.  `stream`: not the legacy default stream. */
+/* Autotuner of the batch's schedule.  First it measures one iteration of
+ * each member alone; a member on the CUDA-core sampler with at most 2048
+ * hidden units is timed in both of its layouts (16 samples per CTA, and the
+ * wide one of VQMC_SAMPLER_CUDA_CORE_WIDE) and keeps the faster.  Then it
+ * times one captured batched iteration (graph replays) under each candidate
+ * schedule -- 1, 2, 4, ... up to the batch's internal streams, with members
+ * assigned round-robin in index order or longest first onto the
+ * least-loaded stream -- and keeps the fastest schedule, with its captured
+ * graph (one iteration, for vqmc_batch_graph_launch).  The iterations it
+ * times are ordinary iterations of every member: each member advances by
+ * 4 + 4 x (number of candidate schedules) iterations.  streams_out and ms_out (NULL allowed) receive the
+ * chosen number of streams and its device time per batched iteration.
+ * `stream`: not the legacy default stream. */
 vqmc_status vqmc_batch_autotune(vqmc_batch* batch, const int32_t* B, vqmc_stream stream, int32_t* streams_out,
                                 double* ms_out);
+
+/* The batch's current schedule: the internal streams in use (streams_used),
+ * and per member (arrays of `count`, each NULL allowed) its stream, its
+ * sampler (VQMC_SAMPLER_TENSOR_CORE, _CUDA_CORE or _CUDA_CORE_WIDE) and the
+ * device time of one of its iterations alone measured by the last
+ * vqmc_batch_autotune (0 before any).  The longest of those times is a lower
+ * bound on a batched iteration (each member's kernels run in order), and
+ * their sum is the time of the members stepped one after another. */
+vqmc_status vqmc_batch_schedule(const vqmc_batch* batch, int32_t* streams_used, int32_t* member_stream,
+                                int32_t* member_sampler, double* member_ms);
 
 /* Device pointers to the last vqmc_step's samples (int8 [B][n]) and energies
  * (int32/float32 [B]); owned by the context, overwritten by the next step. */

@@ -255,16 +255,18 @@ __global__ void split_kernel(int n, int np, const float* __restrict__ J, bf16* _
   }
 }
 
-int grid_for(long long work, int block = 256) {
+// grid-stride launches: at most 32 CTAs of `block` threads per SM of the device
+int grid_for(const vqmc_ctx* c, long long work, int block = 256) {
   long long g = (work + block - 1) / block;
-  if (g > 152 * 32) g = 152 * 32;
+  const long long cap = 32ll * (c->num_sms > 0 ? c->num_sms : 1);
+  if (g > cap) g = cap;
   return (int)(g < 1 ? 1 : g);
 }
 
 template <typename T>
 cudaError_t refresh(vqmc_ctx* c, cudaStream_t st) {
   const int rows = sampler_rows(c->n);
-  rows_kernel<T><<<grid_for((long long)rows * c->hp), 256, 0, st>>>(c->n, c->h, c->hp, rows, c->theta, (T*)c->wt_s,
+  rows_kernel<T><<<grid_for(c, (long long)rows * c->hp), 256, 0, st>>>(c->n, c->h, c->hp, rows, c->theta, (T*)c->wt_s,
                                                                     (T*)c->v_s);
   dim3 grid((c->np + 31) / 32, (c->h + 31) / 32), block(32, 8);
   transpose_kernel<T><<<grid, block, 0, st>>>(c->n, c->h, c->np, c->theta, (T*)c->w_s);
@@ -276,7 +278,7 @@ cudaError_t refresh(vqmc_ctx* c, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_mask_params(vqmc_ctx* c, cudaStream_t st) {
-  mask_kernel<<<grid_for((long long)c->n * c->h), 256, 0, st>>>(c->n, c->h, c->theta);
+  mask_kernel<<<grid_for(c, (long long)c->n * c->h), 256, 0, st>>>(c->n, c->h, c->theta);
   return cudaGetLastError();
 }
 
@@ -338,7 +340,7 @@ cudaError_t launch_prefetch_sampler_weights(const vqmc_ctx* c, cudaStream_t st) 
 }
 
 cudaError_t launch_dense_split(vqmc_ctx* c, cudaStream_t st) {
-  split_kernel<<<grid_for((long long)c->n * c->np), 256, 0, st>>>(c->n, c->np, c->J, (bf16*)c->J_hi, (bf16*)c->J_lo);
+  split_kernel<<<grid_for(c, (long long)c->n * c->np), 256, 0, st>>>(c->n, c->np, c->J, (bf16*)c->J_hi, (bf16*)c->J_lo);
   return cudaGetLastError();
 }
 

@@ -88,6 +88,7 @@ struct vqmc_ctx {
   int act, prec;   // VQMC_ACT_*, VQMC_PREC_*
   int ham;         // VQMC_HAM_*
   int sampler;     // VQMC_SAMPLER_CUDA_CORE or _TENSOR_CORE (resolved at create)
+  int sampler_wide = 0;  // CUDA-core sampler in its four-warp-group layout
   int nnz;
   int64_t d;
   uint64_t inst_hash = 0;
@@ -192,6 +193,11 @@ struct vqmc_ctx {
 
 namespace vqmc {
 
+// ---- sampler_bf16.cu / sampler_f32.cu: whether the CUDA-core sampler runs
+// models with hp padded hidden units and weights of type WT (its register
+// layout and shared-memory ring bound hp), in its default or wide layout
+template <typename WT>
+bool sampler_wt_supports(int hp, bool wide);
 // ---- sampler.cu
 // boff: index of sample 0 in the Philox counter
 cudaError_t launch_uniforms(int B, int n, uint64_t seed, uint64_t iteration, float* d_u, cudaStream_t st,

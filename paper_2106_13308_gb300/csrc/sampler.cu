@@ -69,6 +69,7 @@ cudaError_t launch_sampler(const vqmc_ctx* c, int B, const float* d_u, uint64_t 
   a.logp = d_logp;
   a.err = c->err;
   a.act = c->act;
+  a.wide = c->sampler_wide;
   return c->prec == VQMC_PREC_BF16 ? launch_sampler_wt<bf16>(a, st) : launch_sampler_wt<float>(a, st);
 }
 

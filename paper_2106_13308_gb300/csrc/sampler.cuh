@@ -10,6 +10,7 @@ struct SamplerArgs {
   int n, h, hp, B;
   int act;          // VQMC_ACT_*
   int nst;          // ring stages
+  int wide;         // 1: the four-warp-group layout (4 samples per CTA) at any hp
   const void* wt;   // [n][hp]
   const void* v;    // [n][hp]
   const float* b1;  // [h]
@@ -26,6 +27,7 @@ struct SamplerArgs {
 // Launches the sampler for weights of type WT (float or bf16).
 template <typename WT>
 cudaError_t launch_sampler_wt(const SamplerArgs& a, cudaStream_t st);
+
 
 
 namespace {

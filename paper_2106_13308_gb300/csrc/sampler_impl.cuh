@@ -597,13 +597,27 @@ cudaError_t launch_cfg(const SamplerArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-// Shapes: a group covers GW*32 lanes x 2*U2 units >= hp; 16 samples per CTA.
+// Shapes: a group covers GW*32 lanes x 2*U2 units >= hp; 16 samples per CTA
+// up to hp = 2048.  Beyond, four warps per group and 2 samples per group (4
+// per CTA) keep the pre-activations in about 140 registers per thread; the
+// ring then holds two stages of SPS rows when they fit the shared memory
+// (BF16 up to hp = 5120, FP32 up to hp = 2816).
 template <typename WT>
 cudaError_t launch_sampler_wt(const SamplerArgs& a, cudaStream_t st) {
+  if (a.wide && a.hp <= 5120) return launch_cfg<WT, 4, 2, 20, 2>(a, st);
   if (a.hp <= 64) return launch_cfg<WT, 1, 2, 1, 8>(a, st);
   if (a.hp <= 1024) return launch_cfg<WT, 2, 2, 8, 8>(a, st);
   if (a.hp <= 2048) return launch_cfg<WT, 2, 4, 16, 4>(a, st);
+  if (a.hp <= 5120) return launch_cfg<WT, 4, 2, 20, 2>(a, st);
   return cudaErrorNotSupported;
+}
+
+// Whether launch_sampler_wt<WT> runs models with hp padded hidden units.
+template <typename WT>
+bool sampler_wt_supports(int hp, bool wide) {
+  if (hp <= 2048 && !wide) return true;
+  if (hp <= 5120) return Sampler<WT, 4, 2, 20, 2>::stages_for(hp) >= 2;
+  return false;
 }
 
 }  // namespace vqmc

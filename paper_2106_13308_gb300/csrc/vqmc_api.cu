@@ -227,8 +227,12 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
       if (!(inst->alpha[i] >= 0.0f) || !std::isfinite(inst->alpha[i]))
         return fail(VQMC_ERR_INVALID_ARG, "alpha must be finite and >= 0");
   }
-  if (pad_up(h) > 2048) return fail(VQMC_ERR_UNSUPPORTED, "the samplers support h <= 2048");
-  if (cfg->sampler > VQMC_SAMPLER_TENSOR_CORE) return fail(VQMC_ERR_INVALID_ARG, "bad sampler");
+  if (cfg->sampler > VQMC_SAMPLER_CUDA_CORE_WIDE) return fail(VQMC_ERR_INVALID_ARG, "bad sampler");
+  const bool wide = cfg->sampler == VQMC_SAMPLER_CUDA_CORE_WIDE;
+  if (!(cfg->precision == VQMC_PREC_BF16 ? sampler_wt_supports<bf16>(pad_up(h), wide)
+                                         : sampler_wt_supports<float>(pad_up(h), wide)))
+    return fail(VQMC_ERR_UNSUPPORTED,
+                "the CUDA-core sampler supports h <= 5120 with BF16 weights and h <= 2816 with FP32 weights");
 
   vqmc_ctx* c = new vqmc_ctx();
   c->cfg = *cfg;
@@ -247,8 +251,9 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
       return cleanup_fail(VQMC_ERR_UNSUPPORTED,
                           "tensor-core sampler needs BF16, a tcgen05 device and at most 32 hidden units "
                           "completing within 64 steps");
-    c->sampler = (cfg->sampler != VQMC_SAMPLER_CUDA_CORE && tc_ok) ? VQMC_SAMPLER_TENSOR_CORE
-                                                                      : VQMC_SAMPLER_CUDA_CORE;
+    const bool cc = cfg->sampler == VQMC_SAMPLER_CUDA_CORE || wide;
+    c->sampler = (!cc && tc_ok) ? VQMC_SAMPLER_TENSOR_CORE : VQMC_SAMPLER_CUDA_CORE;
+    c->sampler_wide = wide ? 1 : 0;
   }
 #define VQ_ALLOC(ptr, bytes)                                                                         \
   do {                                                                                               \
@@ -958,6 +963,8 @@ struct vqmc_batch {
   // captured batched iterations (vqmc_batch_graph_capture)
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  // the last autotune's time of one iteration of each member alone (ms)
+  std::vector<double> alone_ms;
 };
 
 namespace {
@@ -1128,27 +1135,48 @@ vqmc_status vqmc_batch_autotune(vqmc_batch* b, const int32_t* B, vqmc_stream str
   if (!stream) return fail(VQMC_ERR_INVALID_ARG, "autotuning captures graphs: pass a non-default stream");
   cudaStream_t st = S(stream);
   const size_t m = b->members.size();
-  // 1. cost of one iteration of each member alone (after one warm-up step)
+  // 1. cost of one iteration of each member alone (after one warm-up step),
+  // and for a member on the CUDA-core sampler up to 2048 hidden units the
+  // faster of its two layouts (16 samples per CTA, or the wide one: groups of
+  // four warps, 4 samples per CTA)
   std::vector<double> cost(m, 0.0);
   {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     VQ_CUDA(cudaEventCreate(&e0));
     VQ_CUDA(cudaEventCreate(&e1));
     vqmc_status s = VQMC_OK;
-    for (size_t i = 0; i < m && s == VQMC_OK; ++i) {
+    auto time_alone = [&](size_t i, float* f) {
       s = vqmc_step(b->members[i], B[i], stream, nullptr);
       if (s == VQMC_OK && cudaEventRecord(e0, st) != cudaSuccess) s = fail(VQMC_ERR_CUDA, "event record failed");
       if (s == VQMC_OK) s = vqmc_step(b->members[i], B[i], stream, nullptr);
       if (s == VQMC_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
         s = fail(VQMC_ERR_CUDA, "event timing failed");
+      *f = 0.0f;
+      if (s == VQMC_OK) cudaEventElapsedTime(f, e0, e1);
+    };
+    for (size_t i = 0; i < m && s == VQMC_OK; ++i) {
+      vqmc_ctx* c = b->members[i];
       float f = 0.0f;
-      if (s == VQMC_OK) cudaEventElapsedTime(&f, e0, e1);
+      time_alone(i, &f);
       cost[i] = f;
+      const bool other = c->sampler == VQMC_SAMPLER_CUDA_CORE && c->hp <= 2048 &&
+                         (c->prec == VQMC_PREC_BF16 ? sampler_wt_supports<bf16>(c->hp, !c->sampler_wide)
+                                                    : sampler_wt_supports<float>(c->hp, !c->sampler_wide));
+      if (s == VQMC_OK && other) {
+        c->sampler_wide ^= 1;
+        time_alone(i, &f);
+        if (s == VQMC_OK && f < cost[i]) cost[i] = f;
+        else c->sampler_wide ^= 1;
+      } else if (s == VQMC_OK) {
+        time_alone(i, &f);  // every member advances by the same number of iterations
+        if (s == VQMC_OK && f < cost[i]) cost[i] = f;
+      }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s != VQMC_OK) return s;
   }
+  b->alone_ms = cost;
   // 2. candidate schedules: 1, 2, 4, 8 streams (up to the batch's), members
   // round-robin in index order or longest-first onto the least-loaded stream
   std::vector<size_t> order(m);
@@ -1189,6 +1217,24 @@ vqmc_status vqmc_batch_autotune(vqmc_batch* b, const int32_t* B, vqmc_stream str
   if (s != VQMC_OK) return s;
   if (streams_out) *streams_out = best_used;
   if (ms_out) *ms_out = best;
+  return VQMC_OK;
+}
+
+vqmc_status vqmc_batch_schedule(const vqmc_batch* b, int32_t* streams_used, int32_t* member_stream,
+                                int32_t* member_sampler, double* member_ms) {
+  if (!b) return fail(VQMC_ERR_INVALID_ARG, "null batch");
+  const size_t m = b->members.size();
+  const size_t k = b->used > 0 ? (size_t)b->used : b->streams.size();
+  if (streams_used) *streams_used = (int32_t)k;
+  for (size_t i = 0; i < m; ++i) {
+    const vqmc_ctx* c = b->members[i];
+    if (member_stream) member_stream[i] = (int32_t)(b->assign.empty() ? i % k : (size_t)b->assign[i]);
+    if (member_sampler)
+      member_sampler[i] = c->sampler == VQMC_SAMPLER_TENSOR_CORE ? VQMC_SAMPLER_TENSOR_CORE
+                          : c->sampler_wide                      ? VQMC_SAMPLER_CUDA_CORE_WIDE
+                                                                 : VQMC_SAMPLER_CUDA_CORE;
+    if (member_ms) member_ms[i] = i < b->alone_ms.size() ? b->alone_ms[i] : 0.0;
+  }
   return VQMC_OK;
 }
 

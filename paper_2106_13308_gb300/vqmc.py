@@ -25,7 +25,8 @@ VQMC_OK, VQMC_ERR_INVALID_ARG, VQMC_ERR_CUDA, VQMC_ERR_OOM = 0, 1, 2, 3
 VQMC_ERR_NONFINITE, VQMC_ERR_TIMEOUT, VQMC_ERR_UNSUPPORTED = 4, 5, 6
 ACT = {"relu": 0, "sigmoid": 1}
 PREC = {"fp32": 0, "bf16": 1}
-SAMPLER = {"auto": 0, "cuda_core": 1, "tensor_core": 2}
+SAMPLER = {"auto": 0, "cuda_core": 1, "tensor_core": 2, "cuda_core_wide": 3}
+SAMPLER_NAME = {v: k for k, v in SAMPLER.items()}
 HAM = {"sparse_i32": 0, "sparse_f32": 1, "dense": 2}
 DEVERR_TIMEOUT, DEVERR_NONFINITE = 1, 2
 
@@ -39,7 +40,7 @@ EXPORTS = [
     "vqmc_batch_count", "vqmc_batch_member", "vqmc_batch_step", "vqmc_sr_gram", "vqmc_sr_direction",
     "vqmc_sr_step", "vqmc_graph_capture", "vqmc_graph_launch", "vqmc_batch_graph_capture",
     "vqmc_batch_graph_launch", "vqmc_batch_autotune", "vqmc_set_sample_offset", "vqmc_shard_sums",
-    "vqmc_shard_apply",
+    "vqmc_shard_apply", "vqmc_batch_schedule",
 ]
 OPT = {"adam": 0, "sr": 1}
 PARTS = ["sample", "energy", "stats", "grad", "adam"]
@@ -126,6 +127,8 @@ def load_library(path: str = LIB_PATH):
         "vqmc_batch_graph_capture": (st, [P, ctypes.POINTER(I32), I32, P]),
         "vqmc_batch_graph_launch": (st, [P, P, ctypes.POINTER(StepStats)]),
         "vqmc_batch_autotune": (st, [P, ctypes.POINTER(I32), P, ctypes.POINTER(I32),
+                                     ctypes.POINTER(ctypes.c_double)]),
+        "vqmc_batch_schedule": (st, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32),
                                      ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
@@ -575,11 +578,23 @@ class VQMCBatch:
         _check(_lib.vqmc_batch_graph_launch(self.handle, _stream(stream), out))
 
     def autotune(self, B, stream=None):
-        """Chooses the schedule (streams, member assignment) by timing graph
-        replays; returns (streams, ms per batched iteration)."""
+        """Chooses each member's sampler layout (timed alone) and the schedule
+        (streams, member assignment) by timing graph replays; returns
+        (streams, ms per batched iteration)."""
         s, ms = ctypes.c_int32(), ctypes.c_double()
         _check(_lib.vqmc_batch_autotune(self.handle, self._bs(B), _stream(stream), ctypes.byref(s), ctypes.byref(ms)))
         return int(s.value), float(ms.value)
+
+    def schedule(self):
+        """(streams in use, [stream of each member], [sampler of each member],
+        [ms of one iteration of each member alone, from the last autotune])."""
+        k = len(self)
+        used = ctypes.c_int32()
+        st = (ctypes.c_int32 * k)()
+        sm = (ctypes.c_int32 * k)()
+        ms = (ctypes.c_double * k)()
+        _check(_lib.vqmc_batch_schedule(self.handle, ctypes.byref(used), st, sm, ms))
+        return int(used.value), list(st), [SAMPLER_NAME[x] for x in sm], list(ms)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -24,6 +24,7 @@ PROBLEMS = [
     (150, 60, 64, "relu", "bf16"),
     (90, 90, 50, "sigmoid", "fp32"),
     (300, 200, 40, "relu", "bf16"),
+    (2300, 2300, 20, "relu", "bf16"),  # more than 2048 hidden units
 ]
 
 

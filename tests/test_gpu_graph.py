@@ -109,21 +109,40 @@ def _make_batch(cfgs, probs):
 
 
 def test_batch_graph_and_autotuned_schedule_equal_eager_batches():
+    """After the autotuner has chosen each member's sampler layout and the
+    schedule, replays of its graph equal eager batched steps of twins with
+    the same samplers, started from the tuned members' state (checkpoints)."""
+    import os
+    import tempfile
     from paper_2106_13308_gb300.vqmc import StepStats
     cfgs, probs = _batch_problems()
     B = [p["max_batch"] for p in probs]
-    tuned, eager = _make_batch(cfgs, probs), _make_batch(cfgs, probs)
+    tuned = _make_batch(cfgs, probs)
     stream = torch.cuda.Stream()
     outs_t = (StepStats * len(probs))()
     outs_e = (StepStats * len(probs))()
     with torch.cuda.stream(stream):
         streams, ms = tuned.autotune(B)
-        assert 1 <= streams <= 6 and ms > 0
-        steps_done = tuned.members[0].iteration
-        assert all(m.iteration == steps_done for m in tuned.members)
+        stream.synchronize()
+    assert 1 <= streams <= 6 and ms > 0
+    steps_done = tuned.members[0].iteration
+    assert all(m.iteration == steps_done for m in tuned.members)
+    used, mstream, samplers, alone = tuned.schedule()
+    assert used == streams and len(mstream) == len(probs) and all(0 <= q < used for q in mstream)
+    assert all(a > 0 for a in alone)
+    # h < n/2 members use the tensor-core sampler; the others one of the two CUDA-core layouts
+    for p, smp in zip(probs, samplers):
+        assert smp == "tensor_core" if p["h"] <= p["n"] // 3 else smp in ("cuda_core", "cuda_core_wide")
+    eager = _make_batch(cfgs, [dict(p, sampler=smp) for p, smp in zip(probs, samplers)])
+    with tempfile.TemporaryDirectory() as d:
+        for q in range(len(probs)):
+            path = os.path.join(d, f"m{q}.ckpt")
+            tuned.members[q].save(path)
+            eager.members[q].load(path)
+    with torch.cuda.stream(stream):
         for _ in range(2):
             tuned.graph_launch(outs_t)
-        for _ in range(steps_done + 2):
+        for _ in range(2):
             eager.step(B, outs_e)
         stream.synchronize()
     for q in range(len(probs)):

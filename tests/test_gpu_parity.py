@@ -50,6 +50,9 @@ CASES = [
     (257, 130, 77, "relu", "bf16", 0.03),
     (129, 500, 33, "relu", "fp32", 0.05),
     (1000, 1000, 64, "relu", "bf16", 0.003),
+    # more than 2048 hidden units: the CUDA-core sampler's four-warp groups, 4 samples per CTA (ragged)
+    (2600, 2600, 13, "relu", "bf16", 0.002),
+    (2200, 2500, 9, "relu", "fp32", 0.002),
 ]
 
 
@@ -343,3 +346,20 @@ def test_adam_matches_oracle(h, prec):
     got = m.get_params().numpy()
     assert np.allclose(got, t0, rtol=0, atol=2e-6)
     assert np.all(got[keep == 0] == 0)
+
+
+@pytest.mark.parametrize("n,h,B,act,prec", [(257, 130, 77, "relu", "bf16"), (300, 200, 30, "relu", "fp32"),
+                                           (20, 40, 64, "sigmoid", "bf16"), (1000, 1000, 9, "relu", "bf16")])
+def test_wide_cuda_core_layout_matches_oracle(n, h, B, act, prec):
+    """The CUDA-core sampler's wide layout (groups of four warps splitting the
+    hidden units, 4 samples per CTA), which the batch autotuner may choose
+    for any member, draws the model's exact samples as the default layout."""
+    inst = er_instance(n, 0.05, 22)
+    theta = inputs.lively_params(n, h, 23)
+    m = make_model(n, h, B, inst, act=act, precision=prec, theta=theta, sampler="cuda_core_wide")
+    P = oracle_params(theta, n, h, prec)
+    U = inputs.uniforms(B, n, 24)
+    S, lp = m.sample(B, torch.from_numpy(U).cuda())
+    S, lp = S.cpu().numpy(), lp.cpu().numpy()
+    _check_samples(P, S, lp, U, act_code(act, prec), prec, f"wide layout n={n} h={h} B={B} {act}")
+    assert m.check() == 0

@@ -288,7 +288,7 @@ _EQ = None
 
 
 @pytest.mark.slow
-@pytest.mark.xfail(strict=False, reason="measured 0.71% (BF16 -48979, FP32 -49331, 5 seeds): at 300 iterations the "
+@pytest.mark.xfail(strict=False, reason="measured 0.77% (BF16 -48952, FP32 -49331, 5 seeds): at 300 iterations the "
                                         "final energy varies by about 2% from seed to seed, so 5 seeds cannot resolve "
                                         "a 0.1% difference")
 def test_bf16_and_fp32_reach_the_same_energy_c3():
@@ -311,3 +311,35 @@ def test_bf16_shows_no_energy_bias_against_fp32_c3():
            z=float(d.mean() / se) if se > 0 else 0.0)
     assert abs(d.mean()) <= 3 * se, (d, se)
     assert r["mean"]["bf16"] < r["initial_mean"] and r["mean"]["fp32"] < r["initial_mean"], r
+
+
+def test_fp32_gradient_estimator_against_fp64_oracle_c3():
+    """The score-function gradient of the plain FP32 path at the benchmark
+    model size (n = 10,000, h = 2,000), 512 samples drawn by the sampler with
+    their energies, against the FP64 oracle's estimator on the same samples.
+    The batch sums of the estimator run in FP32 (the weight-gradient GEMMs
+    accumulate over K = B samples, the bias gradients are FP32 column sums);
+    the coefficients (E_b - mean)/B come from the FP64 mean.  The stated
+    tolerance for FP32 gradients is 1e-4 relative, each parameter block within
+    3x that; the measured errors are reported."""
+    cfg = inputs.config("maxcut_er10000")
+    inst = inputs.make_instance(cfg)
+    n, h = cfg["n"], cfg["h"]
+    Bg = 512
+    theta = inputs.lively_params(n, h, cfg["param_seed"])
+    m = make_model(n, h, Bg, inst, precision="fp32", theta=theta, seed=2026)
+    S, _ = m.sample(Bg, None, iteration=0)
+    E = m.local_energy(S)
+    g, st = m.grad(S, E)
+    g = g.cpu().numpy()
+    P = oracle_params(theta, n, h, "fp32")
+    (dW1, db1, dW2, db2), sto, _ = oracle.vqmc_grad(P, inst, S.cpu().numpy(), act_code("relu", "fp32"))
+    go = oracle.made_to_theta(dW1, db1, dW2, db2)
+    err = rel_err(g, go)
+    from gpu_helpers import grad_blocks
+    blocks = {k: rel_err(v, grad_blocks(go, n, h)[k]) for k, v in grad_blocks(g, n, h).items()}
+    report("fp32 gradient vs fp64 oracle maxcut_er10000 (512 samples)", grad_rel=err, grad_rel_blocks=blocks)
+    assert err <= 1e-4
+    for k, e in blocks.items():
+        assert e <= 3e-4, k
+    assert np.allclose(st.cpu().numpy(), sto, rtol=1e-12)

@@ -221,9 +221,14 @@ def test_exact_gradient_two_routes(act):
 
 def test_batch_gradient_finite_differences():
     """sum_b c_b grad log pi(s_b) against central differences (eps = 1e-3,
-    FP64) of sum_b c_b log pi(s_b) on 32 random parameters of a 3-regular
-    instance; parameters whose +-eps move flips a ReLU are excluded."""
-    n, h, B = 60, 60, 64
+    FP64) of sum_b c_b log pi(s_b) at the random 3-regular workload's model
+    size (n = h = 1000, the sizes of the C2 configuration), on 32 random
+    parameters inside the MADE masks (8 from each of W1, b1, W2, b2) and 16
+    configurations.  A parameter whose +-eps move flips the sign of a hidden
+    pre-activation (a ReLU kink) is excluded; entries outside the masks get
+    exactly zero."""
+    cfg = inputs.config("maxcut_3reg1000")
+    n, h, B = cfg["n"], cfg["h"], 16
     P = _params(n, h, 15)
     S = inputs.spins(B, n, 16)
     coef = np.random.default_rng(17).standard_normal(B) / B
@@ -231,22 +236,33 @@ def test_batch_gradient_finite_differences():
     theta = oracle.made_to_theta(*P)
     m = oracle.degrees(n, h)
     rng = np.random.default_rng(18)
-    live = [q for q in range(theta.size)]
-    idx = rng.choice(live, 32, replace=False)
-
-    def act_signs(th):
-        Q = oracle.theta_to_made(th, n, h)
-        return np.array([oracle.forward(Q, s)[0] > 0 for s in S])
-
-    base = act_signs(theta)
+    nh = n * h
+    # parameters inside the masks: W1^T entry [j][k] (input j+1 feeds unit k iff m(k) >= j+1), b1[k],
+    # W2 entry [i][k] (unit k feeds output i+1 iff i+1 > m(k)), b2[i]
+    jj, kk = np.nonzero(np.arange(1, n + 1)[:, None] <= m[None, :])
+    w1 = rng.choice(jj.size, 8, replace=False)
+    ii, k2 = np.nonzero(np.arange(1, n + 1)[:, None] > m[None, :])
+    w2 = rng.choice(ii.size, 8, replace=False)
+    idx = np.concatenate([jj[w1] * h + kk[w1], nh + rng.choice(h, 8, replace=False),
+                          nh + h + ii[w2] * h + k2[w2], 2 * nh + h + rng.choice(n, 8, replace=False)])
+    # hidden pre-activations of the B configurations (to detect ReLU kinks)
+    W1, b1 = P[0], P[1]
+    mask1 = (np.arange(1, n + 1)[None, :] <= m[:, None])
+    A = S.astype(np.float64) @ (W1 * mask1).T + b1
     eps = 1e-3
     checked = 0
     for q in idx:
+        if q < nh:
+            j, k = divmod(int(q), h)
+            if np.any(np.sign(A[:, k] + eps * S[:, j]) != np.sign(A[:, k] - eps * S[:, j])):
+                continue
+        elif q < nh + h:
+            k = int(q) - nh
+            if np.any(np.sign(A[:, k] + eps) != np.sign(A[:, k] - eps)):
+                continue
         tp, tm = theta.copy(), theta.copy()
         tp[q] += eps
         tm[q] -= eps
-        if not (np.array_equal(act_signs(tp), base) and np.array_equal(act_signs(tm), base)):
-            continue
         fp = coef @ oracle.logprob(oracle.theta_to_made(tp, n, h), S)
         fm = coef @ oracle.logprob(oracle.theta_to_made(tm, n, h), S)
         fd = (fp - fm) / (2 * eps)
@@ -254,9 +270,10 @@ def test_batch_gradient_finite_differences():
         checked += 1
     assert checked >= 24
     # entries outside the masks get exactly zero
-    W1g = g[: n * h].reshape(n, h)  # W1^T layout: [j][k]
-    for j in range(n):
-        assert np.all(W1g[j][m < j + 1] == 0)
+    W1g = g[: nh].reshape(n, h)  # W1^T layout: [j][k]
+    assert np.all(W1g[~(np.arange(1, n + 1)[:, None] <= m[None, :])] == 0)
+    W2g = g[nh + h: 2 * nh + h].reshape(n, h)
+    assert np.all(W2g[~(np.arange(1, n + 1)[:, None] > m[None, :])] == 0)
 
 
 # --------------------------------------------------------------- sampling
