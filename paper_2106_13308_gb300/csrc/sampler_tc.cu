@@ -58,7 +58,15 @@ constexpr int kMaxHp = 2048;               // hidden units (padded) in TMEM
 constexpr int kDmax = 128;
 constexpr int kTmemCols = 512;             // A: 16 per 128 units (<= 256), Z at 256
 constexpr int kZCol = 256;
-constexpr int kThreads = 192;
+constexpr int kThreads = 256;
+// The solver: kLanes lanes per sample on warps 2, 3, 6 and 7 (two warps on
+// each of the sub-partitions that do not host the producer and MMA warps).
+constexpr int kLanes = 8;
+constexpr int kSolverThreads = kS * kLanes;
+// named barriers: 1 = warps 0-3 and the solver warps, 2 = warps 0-1 (arrive)
+// with the solver warps (sync)
+constexpr int kBar1Threads = 128 + 64;
+constexpr int kBar2Threads = 64 + kSolverThreads;
 constexpr int kZld = kS + 1;               // padded row of the Z buffer
 constexpr uint32_t kIdesc = idesc_bf16(128, kS);
 
@@ -145,10 +153,11 @@ __device__ __forceinline__ float g1f(float a) {
 // t_r the step whose spin is recent unit r's last input.  So the steps
 // between two completions, (t_{r-1}, t_r], are conditionally independent
 // given g1_0 .. g1_{r-1}: they form one segment, drawn in parallel.  Lane q
-// draws the steps e = q (mod 4) and keeps, for all 32 recent units, its own
-// partial pre-activation sum over the spins it drew (lane 0 also holds the
-// value at the start of the block).  When segment r ends, unit r's four
-// partials are added with two shuffles, and g1_r = bf16(act(a_r)) enters
+// of the sample's kLanes draws the steps e = q (mod kLanes) and keeps, for
+// all 32 recent units, its own partial pre-activation sum over the spins it
+// drew (lane 0 also holds the value at the start of the block).  When
+// segment r ends, unit r's partials are added with log2(kLanes) shuffles,
+// and g1_r = bf16(act(a_r)) enters
 // the logits of the later segments.  The chain from one completion to the
 // next is: the shuffle reduction, the activation and the rounding, one FMA
 // with W2_{e,r} (the rest of the lane's next logit is summed before the
@@ -156,7 +165,7 @@ __device__ __forceinline__ float g1f(float a) {
 // is zero for units not complete before step e and W1 for inputs after a
 // unit's last one, so no masks are applied; g1 is zero (HH) until a unit
 // completes.  HH holds each sample's recent g1 in shared memory (written by
-// all four lanes with the same value).
+// all the sample's lanes with the same value).
 template <int ACT, bool LP>
 __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf16* Wr, const float* Zs,
                                       const float* LG, const int* TC, uint32_t* SB, float* HH, unsigned char* Hr,
@@ -165,8 +174,8 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
   float P[kRmax];
 #pragma unroll
   for (int k = 0; k < kRmax; ++k) P[k] = q == 0 ? Pr[k * kS + s_me] : 0.0f;
-  reinterpret_cast<float4*>(hh)[2 * q] = make_float4(0.f, 0.f, 0.f, 0.f);
-  reinterpret_cast<float4*>(hh)[2 * q + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  static_assert(kLanes == 8 && kRmax == 32, "hh is zeroed as one float4 per lane");
+  reinterpret_cast<float4*>(hh)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncwarp();
   uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;  // this lane's drawn spins: bit e % 32 of word e / 32
   // Z_e + b2 + the terms of the recent units completed so far (hh)
@@ -221,21 +230,21 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
   for (int r = 0; r <= R; ++r) {  // segment r: steps [lo, hi], units 0 .. r-1 complete
     const int hi = r < R ? TC[r] : steps - 1;
     if (r > 0) hh[r - 1] = g_last;
-    int e = lo + ((q - lo) & 3);
+    int e = lo + ((q - lo) & (kLanes - 1));
     if (e <= hi) {
       draw(e, pf ? fmaf(vn, g_last, zp) : zdot(e));
-      for (e += 4; e <= hi; e += 4) draw(e, zdot(e));
+      for (e += kLanes; e <= hi; e += kLanes) draw(e, zdot(e));
     }
     if (r == R) break;
     // the next segment's first step of this lane, without unit r
     const int nlo = hi + 1, nhi = r + 1 < R ? TC[r + 1] : steps - 1;
-    const int en = nlo + ((q - nlo) & 3);
+    const int en = nlo + ((q - nlo) & (kLanes - 1));
     pf = en <= nhi;
     if (pf) {
       zp = zdot(en);
       vn = __bfloat162float(Vr[en * kLdW + r]);
     }
-    // unit r completes: its partial sums of the four lanes (a binary select of P[r])
+    // unit r completes: the partial sums of the sample's lanes (a binary select of P[r])
     float x;
     {
       float l1[16], l2[8], l3[4], l4[2];
@@ -249,14 +258,14 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
       for (int k = 0; k < 2; ++k) l4[k] = (r & 8) ? l3[2 * k + 1] : l3[2 * k];
       x = (r & 16) ? l4[1] : l4[0];
     }
-    x += __shfl_xor_sync(0xffffffffu, x, 1);
-    x += __shfl_xor_sync(0xffffffffu, x, 2);
+#pragma unroll
+    for (int d = 1; d < kLanes; d <<= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
     g_last = bf16r(g1f<ACT>(x));
     lo = nlo;
   }
-  // the sample's spins: the four lanes' words combined; lane q stores word q
+  // the sample's spins: its lanes' words combined; lane q < 4 stores word q
 #pragma unroll
-  for (int d = 1; d <= 2; d <<= 1) {
+  for (int d = 1; d < kLanes; d <<= 1) {
     w0 |= __shfl_xor_sync(0xffffffffu, w0, d);
     w1 |= __shfl_xor_sync(0xffffffffu, w1, d);
     w2 |= __shfl_xor_sync(0xffffffffu, w2, d);
@@ -266,10 +275,10 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
   // every recent unit is complete: its g1 goes to the staging operand Hr
   // (2 chunks of 64 units from chunk klo / 64), once warps 0-1 have moved
   // the previous block's recent g1 out of it
-  asm volatile("bar.sync 2, 128;" ::: "memory");
+  asm volatile("bar.sync 2, %0;" ::"n"(kBar2Threads) : "memory");
 #pragma unroll
-  for (int j = 0; j < kRmax / 4; ++j) {
-    const int r = q + 4 * j;
+  for (int j = 0; j < kRmax / kLanes; ++j) {
+    const int r = q + kLanes * j;
     if (r < R) {
       const int k = klo + r;
       *reinterpret_cast<bf16*>(Hr + ((k >> 6) - (klo >> 6)) * 2048 + sw128_offset(s_me, k & 63)) =
@@ -347,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(smem_u32(&empty[s]), 1);
     }
     mbar_init(smem_u32(zfull), 1);
-    mbar_init(smem_u32(ready), 64);
+    mbar_init(smem_u32(ready), kSolverThreads);
     mbar_init(smem_u32(merged), 64);
     mbar_init(smem_u32(drain), 1);
     *abort = 0;
@@ -493,12 +502,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(smem_u32(drain), 0u, g.err);
     }
   } else {
-    // ------------------------------------------- warps 0-3: blocks, solver
-    // Warps 2-3 are the solver (on the two SM sub-partitions that do not
-    // also host the producer and MMA warps: warp w runs on w % 4); warps 0-1
-    // meanwhile prepare the next block's logits and write out the previous
-    // block's spins.
-    const int s_me = (tid - 64) >> 2, sub = tid & 3;
+    // ---------------------------- warps 0-3 and 6-7: blocks, solver
+    // Warps 2, 3, 6 and 7 are the solver (two warps on each of the SM
+    // sub-partitions that do not also host the producer and MMA warps: warp w
+    // runs on w % 4); warps 0-3 read tensor memory; warps 0-1 meanwhile
+    // prepare the next block's logits and write out the previous block's
+    // spins.
+    const bool solver = warp == 2 || warp == 3 || warp >= 6;
+    const int sid = (warp == 2 ? 0 : warp == 3 ? 1 : warp == 6 ? 2 : 3) * 32 + lane;  // solver thread
+    const int s_me = sid / kLanes, sub = sid % kLanes;
     float lp = 0.0f;
     const uint32_t tq = tmem + ((uint32_t)(32 * warp) << 16);
     // logit(u) of block b's steps into LG buffer b & 1; threads t0, t0 + nt, ...
@@ -619,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     };
-    logits(0, tid, 128);
+    if (warp < 4) logits(0, tid, 128);
     if (warp < 2) {
       gather_load(0, tid);
       gather_store(0, tid);
@@ -629,6 +641,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int klo = B.klo, khi = B.khi;
       const int R = khi - klo;  // <= kRmax (checked by the host)
       const int steps = min(D, n - b * D);
+      if (warp < 4) {
       // (a) the recent units' completion steps (their weights are in Vr / Wr)
       for (int q = tid; q < (kRmax - R) * kS; q += 128) Pr[R * kS + q] = 0.0f;
       // TC[r] = the block step whose spin is recent unit r's last input
@@ -666,10 +679,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       fence_before();  // the tensor-memory reads precede the next MMAs into Z (after merged)
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      // (c) the D draws of the block (warps 2-3), then the block's spins as
-      // the update GEMM's operand; warps 0-1 meanwhile
-      if (warp >= 2) {
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(kBar1Threads) : "memory");
+      // (c) the D draws of the block (the solver warps), then the block's
+      // spins as the update GEMM's operand; warps 0-1 meanwhile
+      if (solver) {
         const bool relu = g.act == VQMC_ACT_RELU;
         const float* L = LG + (b & 1) * kDrows * kS;
         uint32_t* sb = SB + (b & 1) * kS * (kDmax / 32);
@@ -680,10 +694,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (relu) solve<VQMC_ACT_RELU, false>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, Hr, s_me, sub, klo, R, steps, lp);
           else solve<VQMC_ACT_SIGMOID, false>(Pr, Vr, Wr, Zs, L, CU, sb, PreS, Hr, s_me, sub, klo, R, steps, lp);
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        asm volatile("bar.sync 1, %0;" ::"n"(kBar1Threads) : "memory");
         // (d) 8 spins of one sample per 16-byte store (+1 = 0x3F80, -1 = 0xBF80)
         unsigned char* ss = Ss + (b & 1) * (kDmax / 64) * 2048;
-        for (int q = tid - 64; q < kS * (D / 8); q += 64) {
+        for (int q = sid; q < kS * (D / 8); q += kSolverThreads) {
           const int s = q / (D / 8), e = 8 * (q % (D / 8));
           const uint32_t bits = ~(sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31));  // bit set: spin -1
           uint32_t w[4];
@@ -712,21 +726,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_proxy_async();
         fence_before();
         mbar_arrive(smem_u32(merged));
-        asm volatile("bar.arrive 2, 128;" ::: "memory");
+        asm volatile("bar.arrive 2, %0;" ::"n"(kBar2Threads) : "memory");
         if (b + 1 < nblk) logits(b + 1, tid, 64);
         if (b > 0) write_spins(b - 1, tid, 64);
         if (b + 1 < nblk) gather_load(b + 1, tid);
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        asm volatile("bar.sync 1, %0;" ::"n"(kBar1Threads) : "memory");
         if (b + 1 < nblk) gather_store(b + 1, tid);
       }
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    write_spins(nblk - 1, tid, 128);
-    if (warp >= 2) {  // the four lanes' partial sums of log pi
-      lp += __shfl_xor_sync(0xffffffffu, lp, 1);
-      lp += __shfl_xor_sync(0xffffffffu, lp, 2);
+    asm volatile("bar.sync 1, %0;" ::"n"(kBar1Threads) : "memory");
+    if (warp < 4) write_spins(nblk - 1, tid, 128);
+    if (solver) {  // the partial sums of log pi of the sample's lanes
+#pragma unroll
+      for (int d = 1; d < kLanes; d <<= 1) lp += __shfl_xor_sync(0xffffffffu, lp, d);
     }
-    if (warp >= 2 && sub == 0 && g.logp && b0 + s_me < g.B && !*abort) g.logp[b0 + s_me] = lp;
+    if (solver && sub == 0 && g.logp && b0 + s_me < g.B && !*abort) g.logp[b0 + s_me] = lp;
   }
 
   __syncwarp();
