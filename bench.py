@@ -122,9 +122,16 @@ def _workload(name):
 
 def _config_json(cfg, inst, world, precision_note):
     nnz = int(len(inst["col"])) if inst["kind"] != "dense" else cfg["n"] * (cfg["n"] - 1) // 2
+    wt = {"int1_10": "uniform in {1..10}", "pm1": "+-1", "unit": "1"}.get(cfg.get("weights"), cfg.get("weights"))
+    deg = cfg.get("p", 0) * (cfg["n"] - 1)
+    pstr = f"{round(deg)}/{cfg['n'] - 1}" if abs(deg - round(deg)) < 1e-9 else f"{cfg.get('p', 0):.6g}"
+    graph = {"er": f"Max-Cut on Erdos-Renyi G(n={cfg['n']}, p={pstr}), {nnz} edges, weights {wt} (int32 CSR)",
+             "regular": f"Max-Cut on a random {cfg.get('d')}-regular graph, n={cfg['n']}, {nnz} edges, weights "
+                        f"{wt} (int32 CSR)",
+             "sk": f"Sherrington-Kirkpatrick spin glass, n={cfg['n']}, dense J ~ N(0, 1/n) float32",
+             "tim": f"transverse-field Ising model, n={cfg['n']}, dense"}.get(cfg["graph"], cfg["graph"])
     return {
-        "workload": f"{cfg['name']}: Max-Cut on Erdos-Renyi G(n={cfg['n']}, p=8/9999), {nnz} edges, "
-                    f"weights uniform in {{1..10}} (int32 CSR); MADE h={cfg['h']} {cfg['act']}; "
+        "workload": f"{cfg['name']}: {graph}; MADE h={cfg['h']} {cfg['act']}; "
                     f"batch {cfg['B']} exact samples per step; Adam lr 1e-2",
         "n": cfg["n"], "h": cfg["h"], "batch": cfg["B"], "edges": nnz,
         "precision": precision_note,
@@ -397,6 +404,21 @@ def _batched_arm(K, W, dist_on, world):
     graph_ms, val = _replica_rate(graph_ms_total, K, world, "cuda")
     used, mstream, samplers, alone = batch.schedule()
     ns = [c["n"] for c in cfgs]
+    # the batch's work at the GPU's peaks: the samplers' h n multiply-adds per sample on the FP32 pipe
+    # (CUDA-core samplers, h = n), the five masked log-prob/adjoint GEMMs (about B h n multiply-adds each)
+    # at the sustained BF16 peak, and Adam's 28 bytes per unmasked weight (about h n) at the copy bandwidth
+    fp32_peak, _, _ = _fp32_peak()
+    bf16_peak, _ = _bf16_peak()
+    try:
+        hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]) * 1e9
+    except (OSError, KeyError, ValueError):
+        hbm = 6.8e12
+    fs = sum(2.0 * p["h"] * p["n"] * p["max_batch"] for p in probs)
+    fg = sum(5 * 2.0 * p["h"] * p["n"] * p["max_batch"] / 2 for p in probs)
+    by = sum(28.0 * p["h"] * p["n"] for p in probs)
+    bound_terms = {"sampler_ms": fs / (fp32_peak * 1e12) * 1e3, "gemm_ms": fg / (bf16_peak * 1e12) * 1e3,
+                   "adam_ms": by / hbm * 1e3}
+    bound_ms = sum(bound_terms.values())
     out = {"workload": f"{len(cfgs)} Max-Cut instances, n ~ U{{100..5000}} (min {min(ns)}, max {max(ns)}), "
                        "G(n, 6/(n-1)), weights +-1, MADE h = n relu, 512 samples each, BF16, Adam",
            "value": val, "unit": "batched it/s", "ms_per_step": graph_ms / K,
@@ -407,6 +429,8 @@ def _batched_arm(K, W, dist_on, world):
            # each member's kernels run in order, so the longest member alone bounds a batched iteration
            "bound_ms_longest_member_alone": max(alone), "serial_ms_members_one_after_another": sum(alone),
            "fraction_of_bound": max(alone) / (graph_ms / K),
+           "bound_ms_throughput": bound_ms, "bound_throughput_terms": bound_terms,
+           "fraction_of_throughput_bound": bound_ms / (graph_ms / K),
            "device_error_flags": int(any(flags))}
     batch.close()
     return out
