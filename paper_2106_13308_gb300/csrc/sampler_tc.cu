@@ -223,43 +223,95 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
       P[8 * c + 7] = fmaf(bf_hi(w.w), sv, P[8 * c + 7]);
     }
   };
-  float g_last = 0.0f;       // g1 of the unit that completed last
-  bool pf = false;           // this lane's first step of the segment was prepared
-  float zp = 0.0f, vn = 0.0f;  // ... its logit without the last unit, and that unit's weight on it
+  // the partial sum of unit r among this lane's 32 (a binary select by r)
+  auto extract = [&](int r) -> float {
+    float l1[16], l2[8], l3[4], l4[2];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) l1[k] = (r & 1) ? P[2 * k + 1] : P[2 * k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) l2[k] = (r & 2) ? l1[2 * k + 1] : l1[2 * k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) l3[k] = (r & 4) ? l2[2 * k + 1] : l2[2 * k];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) l4[k] = (r & 8) ? l3[2 * k + 1] : l3[2 * k];
+    return (r & 16) ? l4[1] : l4[0];
+  };
+  auto wt = [&](int e, int r) { return r < kRmax ? __bfloat162float(Wr[e * kLdW + r]) : 0.0f; };
+  auto vt = [&](int e, int r) { return r >= 0 ? __bfloat162float(Vr[e * kLdW + r]) : 0.0f; };
+  auto allsum = [&](float x) {
+#pragma unroll
+    for (int d = 1; d < kLanes; d <<= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+    return x;
+  };
+  // Prepared for this lane's step e of the current segment r (when the
+  // segment has at most kLanes steps, a lane has at most one): its logit
+  // without the unit completed last (zp), that unit's weight on it (vn),
+  // logit(u) (lgn), unit r's weight on its spin (wn) and the lane's partial
+  // sum of unit r over the earlier segments (xr).  Everything else of a
+  // segment runs beside the chain of the completions.
+  float g_last = 0.0f;  // g1 of the unit that completed last
   int lo = 0;
+  int e = q;
+  float zp = 0.0f, vn = 0.0f, lgn = 0.0f, wn = 0.0f, xr = 0.0f;
+  {
+    const int hi0 = R > 0 ? TC[0] : steps - 1;
+    if (e <= hi0) zp = zdot(e), lgn = LG[e * kS + s_me], wn = wt(e, 0);
+    xr = extract(0);
+  }
   for (int r = 0; r <= R; ++r) {  // segment r: steps [lo, hi], units 0 .. r-1 complete
     const int hi = r < R ? TC[r] : steps - 1;
     if (r > 0) hh[r - 1] = g_last;
-    int e = lo + ((q - lo) & (kLanes - 1));
-    if (e <= hi) {
-      draw(e, pf ? fmaf(vn, g_last, zp) : zdot(e));
-      for (e += kLanes; e <= hi; e += kLanes) draw(e, zdot(e));
+    float x;
+    if (hi - lo + 1 <= kLanes) {
+      // ---- at most one step per lane: the chain, then the rest
+      const bool own = e <= hi;
+      const float z = fmaf(vn, g_last, zp);
+      const bool up = z > lgn;
+      const float sv = own ? (up ? 1.0f : -1.0f) : 0.0f;
+      x = fmaf(wn, sv, xr);
+      if (r < R) x = allsum(x);
+      const uint32_t m = (own && up) ? 1u << (e & 31) : 0u;
+      const int wd = e >> 5;
+      w0 |= wd == 0 ? m : 0u;
+      w1 |= wd == 1 ? m : 0u;
+      w2 |= wd == 2 ? m : 0u;
+      w3 |= wd == 3 ? m : 0u;
+      if constexpr (LP) lp += own ? log_sigmoid(up ? z : -z) : 0.0f;
+      if (own) {
+        const uint4* wr = reinterpret_cast<const uint4*>(Wr + e * kLdW);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const uint4 w = wr[c];
+          P[8 * c + 0] = fmaf(bf_lo(w.x), sv, P[8 * c + 0]);
+          P[8 * c + 1] = fmaf(bf_hi(w.x), sv, P[8 * c + 1]);
+          P[8 * c + 2] = fmaf(bf_lo(w.y), sv, P[8 * c + 2]);
+          P[8 * c + 3] = fmaf(bf_hi(w.y), sv, P[8 * c + 3]);
+          P[8 * c + 4] = fmaf(bf_lo(w.z), sv, P[8 * c + 4]);
+          P[8 * c + 5] = fmaf(bf_hi(w.z), sv, P[8 * c + 5]);
+          P[8 * c + 6] = fmaf(bf_lo(w.w), sv, P[8 * c + 6]);
+          P[8 * c + 7] = fmaf(bf_hi(w.w), sv, P[8 * c + 7]);
+        }
+      }
+    } else {
+      // ---- a long segment: every step of the lane with its full logit,
+      // then unit r's partial sums
+      for (int ee = lo + ((q - lo) & (kLanes - 1)); ee <= hi; ee += kLanes) draw(ee, zdot(ee));
+      x = extract(r);
+      if (r < R) x = allsum(x);
     }
     if (r == R) break;
-    // the next segment's first step of this lane, without unit r
+    // prepare this lane's step of segment r + 1 (hh holds units 0 .. r-1)
     const int nlo = hi + 1, nhi = r + 1 < R ? TC[r + 1] : steps - 1;
-    const int en = nlo + ((q - nlo) & (kLanes - 1));
-    pf = en <= nhi;
-    if (pf) {
-      zp = zdot(en);
-      vn = __bfloat162float(Vr[en * kLdW + r]);
+    e = nlo + ((q - nlo) & (kLanes - 1));
+    if (e <= nhi) {
+      zp = zdot(e);
+      vn = vt(e, r);
+      lgn = LG[e * kS + s_me];
+      wn = wt(e, r + 1);
+    } else {
+      zp = 0.0f, vn = 0.0f, lgn = 0.0f, wn = 0.0f;
     }
-    // unit r completes: the partial sums of the sample's lanes (a binary select of P[r])
-    float x;
-    {
-      float l1[16], l2[8], l3[4], l4[2];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) l1[k] = (r & 1) ? P[2 * k + 1] : P[2 * k];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) l2[k] = (r & 2) ? l1[2 * k + 1] : l1[2 * k];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) l3[k] = (r & 4) ? l2[2 * k + 1] : l2[2 * k];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) l4[k] = (r & 8) ? l3[2 * k + 1] : l3[2 * k];
-      x = (r & 16) ? l4[1] : l4[0];
-    }
-#pragma unroll
-    for (int d = 1; d < kLanes; d <<= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+    xr = extract(r + 1 < kRmax ? r + 1 : kRmax - 1);
     g_last = bf16r(g1f<ACT>(x));
     lo = nlo;
   }
