@@ -24,10 +24,11 @@
 // an update adds nothing to a complete unit and an incomplete unit (g1 = 0
 // in shared memory until it completes) adds nothing to any logit.
 //
-// CTA = 16 samples, 6 warps: warps 0-3 own TMEM lanes 32w..32w+31 (read Z
-// and the recent pre-activations); warps 2-3 are the solver (4 lanes per
-// sample, 8 recent units per lane) and then write the block's spins as the
-// update GEMM's operand; while they solve, warps 0-1 merge the previous
+// CTA = 16 samples, 8 warps: warps 0-3 own TMEM lanes 32w..32w+31 (read Z
+// and the recent pre-activations); warps 0, 1, 6 and 7 are the solver (8
+// lanes per sample, each lane owning every 8th step of a segment and partial
+// sums of all the block's recent units) and then write the block's spins as
+// the update GEMM's operand; while they solve, warps 2-3 merge the previous
 // block's recent g1 into the Z operand, prepare the next block's logits and
 // recent-unit weights and write out the previous block's spins; warp 4 lane 0
 // streams 128 x 64 BF16 weight tiles with TMA into a 6-stage ring; warp 5
@@ -59,11 +60,11 @@ constexpr int kDmax = 128;
 constexpr int kTmemCols = 512;             // A: 16 per 128 units (<= 256), Z at 256
 constexpr int kZCol = 256;
 constexpr int kThreads = 256;
-// The solver: kLanes lanes per sample on warps 2, 3, 6 and 7 (two warps on
-// each of the sub-partitions that do not host the producer and MMA warps).
+// The solver: kLanes lanes per sample on warps 0, 1, 6 and 7 (one warp on
+// each SM sub-partition).
 constexpr int kLanes = 8;
 constexpr int kSolverThreads = kS * kLanes;
-// named barriers: 1 = warps 0-3 and the solver warps, 2 = warps 0-1 (arrive)
+// named barriers: 1 = warps 0-3 and the solver warps, 2 = warps 2-3 (arrive)
 // with the solver warps (sync)
 constexpr int kBar1Threads = 128 + 64;
 constexpr int kBar2Threads = 64 + kSolverThreads;
@@ -325,7 +326,7 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
   }
   if (q < kDmax / 32) SB[s_me * (kDmax / 32) + q] = q == 0 ? w0 : q == 1 ? w1 : q == 2 ? w2 : w3;
   // every recent unit is complete: its g1 goes to the staging operand Hr
-  // (2 chunks of 64 units from chunk klo / 64), once warps 0-1 have moved
+  // (2 chunks of 64 units from chunk klo / 64), once warps 2-3 have moved
   // the previous block's recent g1 out of it
   asm volatile("bar.sync 2, %0;" ::"n"(kBar2Threads) : "memory");
 #pragma unroll
@@ -555,13 +556,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------------------- warps 0-3 and 6-7: blocks, solver
-    // Warps 2, 3, 6 and 7 are the solver (two warps on each of the SM
-    // sub-partitions that do not also host the producer and MMA warps: warp w
-    // runs on w % 4); warps 0-3 read tensor memory; warps 0-1 meanwhile
-    // prepare the next block's logits and write out the previous block's
-    // spins.
-    const bool solver = warp == 2 || warp == 3 || warp >= 6;
-    const int sid = (warp == 2 ? 0 : warp == 3 ? 1 : warp == 6 ? 2 : 3) * 32 + lane;  // solver thread
+    // Warps 0, 1, 6 and 7 are the solver, one warp on each SM sub-partition
+    // (warp w runs on w % 4): the solver is issue-bound, and the producer and
+    // MMA warps that share sub-partitions 0 and 1 with it issue little.
+    // Warps 0-3 read tensor memory; warps 2-3 meanwhile prepare the next
+    // block's logits and write out the previous block's spins.
+    const bool solver = warp <= 1 || warp >= 6;
+    const int sid = (warp <= 1 ? warp : warp - 4) * 32 + lane;  // solver thread
+    const int ht = tid - 64;                                      // helper thread (warps 2-3)
     const int s_me = sid / kLanes, sub = sid % kLanes;
     float lp = 0.0f;
     const uint32_t tq = tmem + ((uint32_t)(32 * warp) << 16);
@@ -618,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     };
     // The recent units' weights of block bb (W2 rows of its steps, W1 of its
-    // recent units), loaded by warps 0-1 (thread t < 64) into registers
+    // recent units), loaded by warps 2-3 (helper thread t < 64) into registers
     // during the previous block's solver and stored into Vr / Wr once the
     // solver is done.  Vr: thread t owns steps t and t + 64, 5 aligned
     // 16-byte pieces of W2 from unit klo & ~7; Wr: pieces (unit q % 32,
@@ -684,9 +686,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     };
     if (warp < 4) logits(0, tid, 128);
-    if (warp < 2) {
-      gather_load(0, tid);
-      gather_store(0, tid);
+    if (warp == 2 || warp == 3) {
+      gather_load(0, ht);
+      gather_store(0, ht);
     }
     for (int b = 0; b < nblk; ++b) {
       const Blk B = blk_of(b, n, h, D, ntiles, nblk);
@@ -734,7 +736,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       asm volatile("bar.sync 1, %0;" ::"n"(kBar1Threads) : "memory");
       // (c) the D draws of the block (the solver warps), then the block's
-      // spins as the update GEMM's operand; warps 0-1 meanwhile
+      // spins as the update GEMM's operand; warps 2-3 meanwhile
       if (solver) {
         const bool relu = g.act == VQMC_ACT_RELU;
         const float* L = LG + (b & 1) * kDrows * kS;
@@ -767,7 +769,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // to the solver and the operand to the next Z GEMM
         if (b > 0) {
           const int kprev = count_deg_le((b - 1) * D, n, h), cb = kprev >> 6;
-          for (int q = tid; q < (klo - kprev) * kS; q += 64) {
+          for (int q = ht; q < (klo - kprev) * kS; q += 64) {
             const int k = kprev + q / kS, s = q % kS;
             const uint32_t o = sw128_offset(s, k & 63);
             bf16* src = reinterpret_cast<bf16*>(Hr + ((k >> 6) - cb) * 2048 + o);
@@ -779,11 +781,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_before();
         mbar_arrive(smem_u32(merged));
         asm volatile("bar.arrive 2, %0;" ::"n"(kBar2Threads) : "memory");
-        if (b + 1 < nblk) logits(b + 1, tid, 64);
-        if (b > 0) write_spins(b - 1, tid, 64);
-        if (b + 1 < nblk) gather_load(b + 1, tid);
+        if (b + 1 < nblk) logits(b + 1, ht, 64);
+        if (b > 0) write_spins(b - 1, ht, 64);
+        if (b + 1 < nblk) gather_load(b + 1, ht);
         asm volatile("bar.sync 1, %0;" ::"n"(kBar1Threads) : "memory");
-        if (b + 1 < nblk) gather_store(b + 1, tid);
+        if (b + 1 < nblk) gather_store(b + 1, ht);
       }
     }
     asm volatile("bar.sync 1, %0;" ::"n"(kBar1Threads) : "memory");
