@@ -250,27 +250,29 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
   // logit(u) (lgn), unit r's weight on its spin (wn) and the lane's partial
   // sum of unit r over the earlier segments (xr).  Everything else of a
   // segment runs beside the chain of the completions.
+  // The segment body below is free of lane-dependent branches: a lane
+  // without a step in the segment (e past its end) draws nothing (sv = 0)
+  // and reads row min(e, kDrows - 1) of the tables, so that the compiler can
+  // move the next segment's loads ahead of the completion chain.
   float g_last = 0.0f;  // g1 of the unit that completed last
   int lo = 0;
   int e = q;
+  int hi = R > 0 ? TC[0] : steps - 1;  // last step of the current segment
   float zp = 0.0f, vn = 0.0f, lgn = 0.0f, wn = 0.0f, xr = 0.0f;
-  {
-    const int hi0 = R > 0 ? TC[0] : steps - 1;
-    if (e <= hi0) zp = zdot(e), lgn = LG[e * kS + s_me], wn = wt(e, 0);
-    xr = extract(0);
-  }
+  if (e <= hi) zp = zdot(e), lgn = LG[e * kS + s_me], wn = wt(e, 0);
+  xr = extract(0);
   for (int r = 0; r <= R; ++r) {  // segment r: steps [lo, hi], units 0 .. r-1 complete
-    const int hi = r < R ? TC[r] : steps - 1;
-    if (r > 0) hh[r - 1] = g_last;
+    const int nhi = r + 1 < R ? TC[r + 1] : steps - 1;  // last step of segment r + 1
+    hh[r > 0 ? r - 1 : 0] = g_last;                     // (unit 0's entry is still zero at r = 0)
     float x;
     if (hi - lo + 1 <= kLanes) {
       // ---- at most one step per lane: the chain, then the rest
       const bool own = e <= hi;
+      const int el = min(e, kDrows - 1);
       const float z = fmaf(vn, g_last, zp);
       const bool up = z > lgn;
       const float sv = own ? (up ? 1.0f : -1.0f) : 0.0f;
-      x = fmaf(wn, sv, xr);
-      if (r < R) x = allsum(x);
+      x = allsum(fmaf(wn, sv, xr));
       const uint32_t m = (own && up) ? 1u << (e & 31) : 0u;
       const int wd = e >> 5;
       w0 |= wd == 0 ? m : 0u;
@@ -278,8 +280,8 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
       w2 |= wd == 2 ? m : 0u;
       w3 |= wd == 3 ? m : 0u;
       if constexpr (LP) lp += own ? log_sigmoid(up ? z : -z) : 0.0f;
-      if (own) {
-        const uint4* wr = reinterpret_cast<const uint4*>(Wr + e * kLdW);
+      {
+        const uint4* wr = reinterpret_cast<const uint4*>(Wr + el * kLdW);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const uint4 w = wr[c];
@@ -297,24 +299,24 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
       // ---- a long segment: every step of the lane with its full logit,
       // then unit r's partial sums
       for (int ee = lo + ((q - lo) & (kLanes - 1)); ee <= hi; ee += kLanes) draw(ee, zdot(ee));
-      x = extract(r);
-      if (r < R) x = allsum(x);
+      x = allsum(extract(r));
     }
     if (r == R) break;
-    // prepare this lane's step of segment r + 1 (hh holds units 0 .. r-1)
-    const int nlo = hi + 1, nhi = r + 1 < R ? TC[r + 1] : steps - 1;
+    // prepare this lane's step of segment r + 1 (hh holds units 0 .. r-1);
+    // a lane without one (e > nhi) keeps values that its sv = 0 ignores
+    const int nlo = hi + 1;
     e = nlo + ((q - nlo) & (kLanes - 1));
-    if (e <= nhi) {
-      zp = zdot(e);
-      vn = vt(e, r);
-      lgn = LG[e * kS + s_me];
-      wn = wt(e, r + 1);
-    } else {
-      zp = 0.0f, vn = 0.0f, lgn = 0.0f, wn = 0.0f;
+    {
+      const int el = min(e, kDrows - 1);
+      zp = zdot(el);
+      vn = vt(el, r);
+      lgn = LG[el * kS + s_me];
+      wn = wt(el, r + 1);
     }
     xr = extract(r + 1 < kRmax ? r + 1 : kRmax - 1);
     g_last = bf16r(g1f<ACT>(x));
     lo = nlo;
+    hi = nhi;
   }
   // the sample's spins: its lanes' words combined; lane q < 4 stores word q
 #pragma unroll
