@@ -512,6 +512,21 @@ bool tc_encode_bf16(CUtensorMap* map, const void* ptr, int rows, int cols, int l
   return r == CUDA_SUCCESS;
 }
 
+bool tc_encode_bf16_chunks(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows,
+                           int box_chunks) {
+  if (!gemm_tc_available() || cols % BK || box_chunks < 1 || box_chunks > 8) return false;
+  // chunk c of row r starts at element r * ld + 64 c: the view covers
+  // exactly the rows x cols elements of the 2D matrix
+  cuuint64_t dims[3] = {(cuuint64_t)BK, (cuuint64_t)rows, (cuuint64_t)(cols / BK)};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)BK * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)box_chunks};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool gemm_tc_available() {
   std::call_once(g_once, init_once);
   return g_have_tc;

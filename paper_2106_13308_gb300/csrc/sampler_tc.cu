@@ -49,11 +49,14 @@ constexpr int kS = 16;                     // samples per CTA (MMA N)
 constexpr int kRmax = 32;                  // recent units per block
 constexpr int kNStage = 6;                 // weight tiles in the ring
 constexpr int kTileBytes = 128 * 64 * 2;   // one 128 x 64 BF16 tile
-// The ring is consumed in slots of up to two tiles (32 KB): one full-barrier
-// wait and one commit per slot.  The single thread that issues the MMAs pays
-// a fixed cost for every wait and every commit, comparable to the tensor
-// work of an N = 16 tile, so pairing tiles nearly halves the time per tile.
-constexpr int kSlotTiles = 2;
+// The ring is consumed in slots of up to three tiles (48 KB): one
+// full-barrier wait and one commit per slot.  The single thread that issues
+// the MMAs pays a fixed cost for every wait and every commit, comparable to
+// the tensor work of an N = 16 tile, so grouping tiles cuts the time per
+// tile.  A slot's tiles that are consecutive 64-column chunks of the same
+// rows arrive in one copy: the copy engine's time goes by copies more than by
+// bytes (a 32 KB box streams about twice as fast as two 16 KB boxes).
+constexpr int kSlotTiles = 3;
 constexpr int kNSlot = kNStage / kSlotTiles;
 constexpr int kMaxHp = 2048;               // hidden units (padded) in TMEM
 constexpr int kDmax = 128;
@@ -123,6 +126,20 @@ struct TcArgs {
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+// FP32 pairs for fma.rn.f32x2 (two IEEE FP32 FMAs per instruction)
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(uint64_t v, float& lo, float& hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// the two BF16 weights of a word, widened (exactly) to an FP32 pair
+__device__ __forceinline__ uint64_t bf2(uint32_t w) { return pk2(bf_lo(w), bf_hi(w)); }
 
 // bounded wait that gives up at once after any failure in the CTA; with
 // backoff the polling thread sleeps between tries so that it takes no issue
@@ -183,21 +200,37 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
   auto zdot = [&](int e) -> float {
     const uint4* vr = reinterpret_cast<const uint4*>(Vr + e * kLdW);
     const float4* hv = reinterpret_cast<const float4*>(hh);
-    float a0 = Zs[e * kZld + s_me], a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    // four FP32 accumulators a0..a3 as the pairs (a0, a1), (a2, a3)
+    uint64_t a01 = pk2(Zs[e * kZld + s_me], 0.0f), a23 = pk2(0.0f, 0.0f);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const uint4 v = vr[c];
       const float4 x = hv[2 * c], y = hv[2 * c + 1];
-      a0 = fmaf(bf_lo(v.x), x.x, a0);
-      a1 = fmaf(bf_hi(v.x), x.y, a1);
-      a2 = fmaf(bf_lo(v.y), x.z, a2);
-      a3 = fmaf(bf_hi(v.y), x.w, a3);
-      a0 = fmaf(bf_lo(v.z), y.x, a0);
-      a1 = fmaf(bf_hi(v.z), y.y, a1);
-      a2 = fmaf(bf_lo(v.w), y.z, a2);
-      a3 = fmaf(bf_hi(v.w), y.w, a3);
+      a01 = fma2(bf2(v.x), pk2(x.x, x.y), a01);
+      a23 = fma2(bf2(v.y), pk2(x.z, x.w), a23);
+      a01 = fma2(bf2(v.z), pk2(y.x, y.y), a01);
+      a23 = fma2(bf2(v.w), pk2(y.z, y.w), a23);
     }
+    float a0, a1, a2, a3;
+    upk2(a01, a0, a1);
+    upk2(a23, a2, a3);
     return (a0 + a1) + (a2 + a3);
+  };
+  // this lane's partial sums of all recent units += sv * W1 of step row el
+  auto wrow = [&](int el, float sv) {
+    const uint4* wr = reinterpret_cast<const uint4*>(Wr + el * kLdW);
+    const uint64_t s2 = pk2(sv, sv);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint4 w = wr[c];
+      const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint64_t pp = pk2(P[8 * c + 2 * j], P[8 * c + 2 * j + 1]);
+        pp = fma2(bf2(ww[j]), s2, pp);
+        upk2(pp, P[8 * c + 2 * j], P[8 * c + 2 * j + 1]);
+      }
+    }
   };
   // draw of step e from its logit, and the spin into this lane's partial sums
   auto draw = [&](int e, float z) {
@@ -209,20 +242,7 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
     w2 |= wd == 2 ? m : 0u;
     w3 |= wd == 3 ? m : 0u;
     if constexpr (LP) lp += log_sigmoid(up ? z : -z);
-    const float sv = up ? 1.0f : -1.0f;
-    const uint4* wr = reinterpret_cast<const uint4*>(Wr + e * kLdW);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const uint4 w = wr[c];
-      P[8 * c + 0] = fmaf(bf_lo(w.x), sv, P[8 * c + 0]);
-      P[8 * c + 1] = fmaf(bf_hi(w.x), sv, P[8 * c + 1]);
-      P[8 * c + 2] = fmaf(bf_lo(w.y), sv, P[8 * c + 2]);
-      P[8 * c + 3] = fmaf(bf_hi(w.y), sv, P[8 * c + 3]);
-      P[8 * c + 4] = fmaf(bf_lo(w.z), sv, P[8 * c + 4]);
-      P[8 * c + 5] = fmaf(bf_hi(w.z), sv, P[8 * c + 5]);
-      P[8 * c + 6] = fmaf(bf_lo(w.w), sv, P[8 * c + 6]);
-      P[8 * c + 7] = fmaf(bf_hi(w.w), sv, P[8 * c + 7]);
-    }
+    wrow(e, up ? 1.0f : -1.0f);
   };
   // the partial sum of unit r among this lane's 32 (a binary select by r)
   auto extract = [&](int r) -> float {
@@ -280,21 +300,7 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
       w2 |= wd == 2 ? m : 0u;
       w3 |= wd == 3 ? m : 0u;
       if constexpr (LP) lp += own ? log_sigmoid(up ? z : -z) : 0.0f;
-      {
-        const uint4* wr = reinterpret_cast<const uint4*>(Wr + el * kLdW);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const uint4 w = wr[c];
-          P[8 * c + 0] = fmaf(bf_lo(w.x), sv, P[8 * c + 0]);
-          P[8 * c + 1] = fmaf(bf_hi(w.x), sv, P[8 * c + 1]);
-          P[8 * c + 2] = fmaf(bf_lo(w.y), sv, P[8 * c + 2]);
-          P[8 * c + 3] = fmaf(bf_hi(w.y), sv, P[8 * c + 3]);
-          P[8 * c + 4] = fmaf(bf_lo(w.z), sv, P[8 * c + 4]);
-          P[8 * c + 5] = fmaf(bf_hi(w.z), sv, P[8 * c + 5]);
-          P[8 * c + 6] = fmaf(bf_lo(w.w), sv, P[8 * c + 6]);
-          P[8 * c + 7] = fmaf(bf_hi(w.w), sv, P[8 * c + 7]);
-        }
-      }
+      wrow(el, sv);
     } else {
       // ---- a long segment: every step of the lane with its full logit,
       // then unit r's partial sums
@@ -371,7 +377,8 @@ __device__ __forceinline__ Blk blk_of(int b, int n, int h, int D, int ntiles, in
 
 __global__ void __launch_bounds__(kThreads, 1)
     sampler_tc_kernel(const __grid_constant__ CUtensorMap mapV, const __grid_constant__ CUtensorMap mapW,
-                      const TcArgs g) {
+                      const __grid_constant__ CUtensorMap mapV2, const __grid_constant__ CUtensorMap mapV3,
+                      const __grid_constant__ CUtensorMap mapW2, const TcArgs g) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -451,8 +458,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     // b+1's rows).
     if (lane == 0) {
       int it = 0;  // slots issued
-      // the tiles [i0, i1) of one phase, two per slot; xy(i, x, y) gives tile i's box
-      auto load_phase = [&](const CUtensorMap* map, int i0, int i1, auto xy) -> bool {
+      // the tiles [i0, i1) of one phase, kSlotTiles per slot; yc(i, y, c)
+      // gives tile i's first row and 64-column chunk.  A run of tiles with
+      // the same rows and consecutive chunks (at most `most`) is one copy
+      // through the chunked map of its length (m2: 2, m3: 3).
+      auto load_phase = [&](const CUtensorMap* m1, const CUtensorMap* m2, const CUtensorMap* m3, int most, int i0,
+                            int i1, auto yc) -> bool {
         for (int i = i0; i < i1; i += kSlotTiles) {
           const int cnt = min(kSlotTiles, i1 - i);
           const int s = it % kNSlot;
@@ -461,10 +472,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             return false;
           const uint32_t bar = smem_u32(&full[s]);
           mbar_expect_tx(bar, (uint32_t)(cnt * kTileBytes));
-          for (int j = 0; j < cnt; ++j) {
-            int x, y;
-            xy(i + j, x, y);
-            tma_load_2d(base + kOffRing + (s * kSlotTiles + j) * kTileBytes, map, x, y, bar);
+          for (int j = 0; j < cnt;) {
+            int y, c;
+            yc(i + j, y, c);
+            int run = 1;
+            while (j + run < cnt && run < most) {
+              int y2, c2;
+              yc(i + j + run, y2, c2);
+              if (y2 != y || c2 != c + run) break;
+              ++run;
+            }
+            const uint32_t dst = base + kOffRing + (s * kSlotTiles + j) * kTileBytes;
+            if (run == 1) tma_load_2d(dst, m1, 64 * c, y, bar);
+            else tma_load_3d(dst, run == 2 ? m2 : m3, 0, y, c, bar);
+            j += run;
           }
           ++it;
         }
@@ -474,11 +495,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int b = 0; b < nblk && ok; ++b) {
         const Blk B = blk_of(b, n, h, D, ntiles, nblk);
         // update tiles: index q -> unit tile q / nkd, K-chunk q % nkd of block b-1's inputs
-        auto upd = [&](int q, int& x, int& y) { x = (b - 1) * D + 64 * (q % nkd), y = 128 * (q / nkd); };
-        ok = load_phase(&mapW, B.crit0 * nkd, B.crit1 * nkd, upd);
-        if (ok) ok = load_phase(&mapV, B.cor0, B.cor1, [&](int c, int& x, int& y) { x = 64 * c, y = b * D; });
-        if (ok) ok = load_phase(&mapW, B.bulk0 * nkd, ntiles * nkd, upd);
-        if (ok) ok = load_phase(&mapV, 0, B.np, [&](int c, int& x, int& y) { x = 64 * c, y = (b + 1) * D; });
+        auto upd = [&](int q, int& y, int& c) { y = 128 * (q / nkd), c = (b - 1) * (D / 64) + q % nkd; };
+        ok = load_phase(&mapW, &mapW2, &mapW2, 2, B.crit0 * nkd, B.crit1 * nkd, upd);
+        if (ok)
+          ok = load_phase(&mapV, &mapV2, &mapV3, 3, B.cor0, B.cor1, [&](int c, int& y, int& cc) { y = b * D, cc = c; });
+        if (ok) ok = load_phase(&mapW, &mapW2, &mapW2, 2, B.bulk0 * nkd, ntiles * nkd, upd);
+        if (ok)
+          ok = load_phase(&mapV, &mapV2, &mapV3, 3, 0, B.np, [&](int c, int& y, int& cc) { y = (b + 1) * D, cc = c; });
       }
       // no copy may still be landing when the CTA exits (after a failure
       // some loaded tiles are never consumed)
@@ -837,9 +860,14 @@ cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64
   const int D = sampler_tc_block(c);
   if (D == 0 || !gemm_tc_available()) return cudaErrorNotSupported;
   if (B <= 0) return cudaSuccess;
-  CUtensorMap mapV, mapW;
+  // v_s [sampler_rows(n)][hp] and w_s [h][np] (hp, np multiples of 64): one
+  // 128 x 64 tile per copy, or 2 or 3 consecutive chunks of the same rows
+  CUtensorMap mapV, mapW, mapV2, mapV3, mapW2;
   if (!tc_encode_bf16(&mapV, c->v_s, sampler_rows(c->n), c->hp, c->hp, 128) ||
-      !tc_encode_bf16(&mapW, c->w_s, c->h, c->np, c->np, 128))
+      !tc_encode_bf16(&mapW, c->w_s, c->h, c->np, c->np, 128) ||
+      !tc_encode_bf16_chunks(&mapV2, c->v_s, sampler_rows(c->n), c->hp, c->hp, 128, 2) ||
+      !tc_encode_bf16_chunks(&mapV3, c->v_s, sampler_rows(c->n), c->hp, c->hp, 128, 3) ||
+      !tc_encode_bf16_chunks(&mapW2, c->w_s, c->h, c->np, c->np, 128, 2))
     return cudaErrorInvalidValue;
   if (!g_attr_set) {
     cudaError_t e = cudaFuncSetAttribute(sampler_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
@@ -873,7 +901,7 @@ cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64
   a.stt = reinterpret_cast<bf16*>(stt);
   a.ldst = c->Bp;
   a.sbits = reinterpret_cast<uint16_t*>(sbits);
-  sampler_tc_kernel<<<(B + kS - 1) / kS, kThreads, kSmemBytes, st>>>(mapV, mapW, a);
+  sampler_tc_kernel<<<(B + kS - 1) / kS, kThreads, kSmemBytes, st>>>(mapV, mapW, mapV2, mapV3, mapW2, a);
   return cudaGetLastError();
 }
 

@@ -50,6 +50,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// 3D tiled load (x innermost); the box's planes land one after another
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
 // UMMA shared-memory descriptor of a K-major BF16 operand stored with the
 // 128-byte swizzle: rows of 128 bytes (64 elements along K), 8-row groups
 // 1024 bytes apart (stride byte offset), leading byte offset unused (1),
@@ -138,5 +147,10 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t tmem, uint32_t cols) {
 // swizzle, zero fill outside the matrix.  False if the driver rejects it or
 // the tensor-core path is unavailable.
 bool tc_encode_bf16(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows);
+// The same matrix (cols a multiple of 64) viewed as {64 columns, rows, cols /
+// 64 chunks}: one box of box_chunks x (box_rows x 64) is box_chunks
+// consecutive 128B-swizzled tiles of the 2D map above, in one copy.
+bool tc_encode_bf16_chunks(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows,
+                           int box_chunks);
 
 }  // namespace vqmc
