@@ -42,14 +42,32 @@ constexpr int kThreads = 256;
 constexpr int kHalf = BN / 2;  // columns per epilogue thread
 constexpr int TILE_A_BYTES = BM * BK * 2;  // 16 KB
 constexpr int TILE_B_BYTES = BN * BK * 2;  // 16 KB
-constexpr int STAGE_BYTES = TILE_A_BYTES + TILE_B_BYTES;
 constexpr int TMEM_COLS = BN;  // FP32 accumulator: 128 lanes x BN columns
-// tiles | barriers (256) | column partials [4][BN] | bias [BN] | row partials [BM]
-constexpr int kOffBars = NSTAGE * STAGE_BYTES;
-constexpr int kOffCol = kOffBars + 256;
-constexpr int kOffBias = kOffCol + 4 * BN * 4;
-constexpr int kOffRow = kOffBias + BN * 4;
-constexpr int SMEM_BYTES = 1024 /*alignment slack*/ + kOffRow + BM * 4;
+// A stage holds KC consecutive 64-wide K chunks of A and of B: [A chunk
+// 0 .. KC-1][B chunk 0 .. KC-1].  With KC = 1 two CTAs share an SM (one's
+// epilogue runs beside the other's main loop); with KC = 2 each operand's
+// chunks arrive in one 32 KB copy (a 3D view of the operand), which the copy
+// engine streams about twice as fast as two 16 KB copies, and one CTA holds
+// the SM.  Shared memory: tiles | barriers (256) | column partials [4][BN] |
+// bias [BN] | row partials [BM].
+constexpr int kNumOps = 6;
+// K chunks per stage for each GemmOp, chosen by timing both settings at
+// n = 10000, h = 2000, B = 2048: the hidden GEMM and the hidden adjoint gain
+// 2-3% from the larger copies; the ops with heavy epilogues (log pi and the
+// output adjoint, the fused Adam steps) lose 20-30% without a second CTA
+// beside them (dW2 119 -> 144 us, dW1 113 -> 140 us, kOpOut 92 -> 122 us).
+constexpr int kStageChunks[kNumOps] = {2, 1, 1, 2, 1, 1};
+template <int KC>
+struct Stages {
+  static constexpr int kStage = KC * (TILE_A_BYTES + TILE_B_BYTES);
+  static constexpr int kOffBars = NSTAGE * kStage;
+  static constexpr int kOffCol = kOffBars + 256;
+  static constexpr int kOffBias = kOffCol + 4 * BN * 4;
+  static constexpr int kOffRow = kOffBias + BN * 4;
+  static constexpr int kSmem = 1024 /*alignment slack*/ + kOffRow + BM * 4;
+  static constexpr int kMinBlocks = KC == 1 ? 2 : 1;
+  static_assert(kMinBlocks * kSmem <= 232448, "shared memory per SM");
+};
 
 using namespace tc;
 
@@ -204,11 +222,15 @@ __device__ __forceinline__ void wgrad_block(const GemmArgs<bf16>& g, bool fused,
     }
 }
 
-template <int OP>
-__global__ void __launch_bounds__(kThreads, 2) gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
-                                                               const __grid_constant__ CUtensorMap mapB,
-                                                               const __grid_constant__ CUtensorMap mapB2,
-                                                               const GemmArgs<bf16> g, int two_pass) {
+template <int OP, int KC>
+__global__ void __launch_bounds__(kThreads, Stages<KC>::kMinBlocks)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const __grid_constant__ CUtensorMap mapB2, const __grid_constant__ CUtensorMap mapAc,
+                   const __grid_constant__ CUtensorMap mapBc, const __grid_constant__ CUtensorMap mapB2c,
+                   const GemmArgs<bf16> g, int two_pass, int kfull) {
+  using St = Stages<KC>;
+  constexpr int STAGE_BYTES = St::kStage, kOffBars = St::kOffBars, kOffCol = St::kOffCol,
+                kOffBias = St::kOffBias, kOffRow = St::kOffRow;
   uint32_t* err = g.err;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -251,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 2) gemm_tc_kernel(const __grid_const
   gemm_k_range(op, n0, n1, g.K, g.n, g.h, &klo, &khi);
   const int kt0 = klo / BK;
   const int kt1 = (khi + BK - 1) / BK;
-  const int per_pass = kt1 > kt0 ? kt1 - kt0 : 0;
+  const int per_pass = kt1 > kt0 ? (kt1 - kt0 + KC - 1) / KC : 0;  // stages per pass
   const int nkt = per_pass * (two_pass ? 2 : 1);
 
   if (tid == 0) {
@@ -275,12 +297,21 @@ __global__ void __launch_bounds__(kThreads, 2) gemm_tc_kernel(const __grid_const
       const int s = it % NSTAGE;
       if (it >= NSTAGE) ok = mbar_wait(smem_u32(&empty[s]), (uint32_t)((it / NSTAGE - 1) & 1), err);
       if (!ok) break;
-      const int pass = it / per_pass, kt = kt0 + (it - pass * per_pass);
-      const uint32_t sa = base + s * STAGE_BYTES, sb = sa + TILE_A_BYTES;
+      const int pass = it / per_pass, kt = kt0 + KC * (it - pass * per_pass);
+      const int nch = min(KC, kt1 - kt);  // K chunks of this stage
+      const uint32_t sa = base + s * STAGE_BYTES, sb = sa + KC * TILE_A_BYTES;
       const uint32_t bar = smem_u32(&full[s]);
-      mbar_expect_tx(bar, STAGE_BYTES);
-      tma_load_2d(sa, &mapA, kt * BK, m0, bar);
-      tma_load_2d(sb, pass == 0 ? &mapB : &mapB2, kt * BK, n0, bar);
+      mbar_expect_tx(bar, (uint32_t)(nch * (TILE_A_BYTES + TILE_B_BYTES)));
+      if (KC > 1 && nch == KC && kt + KC <= kfull) {
+        // KC whole chunks inside the chunked view (kfull = floor(K / 64))
+        tma_load_3d(sa, &mapAc, 0, m0, kt, bar);
+        tma_load_3d(sb, pass == 0 ? &mapBc : &mapB2c, 0, n0, kt, bar);
+      } else {
+        for (int c = 0; c < nch; ++c) {
+          tma_load_2d(sa + c * TILE_A_BYTES, &mapA, (kt + c) * BK, m0, bar);
+          tma_load_2d(sb + c * TILE_B_BYTES, pass == 0 ? &mapB : &mapB2, (kt + c) * BK, n0, bar);
+        }
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // --------------------------------------------------------- MMA issuer
@@ -289,11 +320,18 @@ __global__ void __launch_bounds__(kThreads, 2) gemm_tc_kernel(const __grid_const
       ok = mbar_wait(smem_u32(&full[s]), (uint32_t)((it / NSTAGE) & 1), err);
       if (!ok) break;
       fence_after();
-      const uint32_t sa = base + s * STAGE_BYTES, sb = sa + TILE_A_BYTES;
-      const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
+      const int pass = it / per_pass, kt = kt0 + KC * (it - pass * per_pass);
+      const int nch = min(KC, kt1 - kt);
+      const uint32_t sa = base + s * STAGE_BYTES, sb = sa + KC * TILE_A_BYTES;
 #pragma unroll
-      for (int k = 0; k < BK / 16; ++k)  // advance 16 BF16 = 32 bytes along K inside the swizzle atom
-        mma_bf16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kIdesc, (it > 0 || k > 0) ? 1u : 0u);
+      for (int c = 0; c < KC; ++c) {
+        if (c >= nch) break;
+        const uint64_t da = smem_desc_sw128(sa + c * TILE_A_BYTES), db = smem_desc_sw128(sb + c * TILE_B_BYTES);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k)  // advance 16 BF16 = 32 bytes along K inside the swizzle atom
+          mma_bf16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), kIdesc,
+                   (it > 0 || c > 0 || k > 0) ? 1u : 0u);
+      }
       mma_commit(smem_u32(&empty[s]));
     }
     if (nkt > 0 && ok) mma_commit(smem_u32(done));
@@ -486,11 +524,17 @@ void init_once() {
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   g_have_tc = g_encode != nullptr && major == 10 && minor == 3;
-  const void* kernels[] = {(const void*)gemm_tc_kernel<kOpHidden>, (const void*)gemm_tc_kernel<kOpOut>,
-                           (const void*)gemm_tc_kernel<kOpDV>, (const void*)gemm_tc_kernel<kOpGA>,
-                           (const void*)gemm_tc_kernel<kOpDW>, (const void*)gemm_tc_kernel<kOpEloc>};
-  for (const void* k : kernels)
-    if (g_have_tc && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
+  const void* k1[] = {(const void*)gemm_tc_kernel<kOpHidden, 1>, (const void*)gemm_tc_kernel<kOpOut, 1>,
+                      (const void*)gemm_tc_kernel<kOpDV, 1>,     (const void*)gemm_tc_kernel<kOpGA, 1>,
+                      (const void*)gemm_tc_kernel<kOpDW, 1>,     (const void*)gemm_tc_kernel<kOpEloc, 1>};
+  const void* k2[] = {(const void*)gemm_tc_kernel<kOpHidden, 2>, (const void*)gemm_tc_kernel<kOpOut, 2>,
+                      (const void*)gemm_tc_kernel<kOpDV, 2>,     (const void*)gemm_tc_kernel<kOpGA, 2>,
+                      (const void*)gemm_tc_kernel<kOpDW, 2>,     (const void*)gemm_tc_kernel<kOpEloc, 2>};
+  for (const void* k : k1)
+    if (g_have_tc && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Stages<1>::kSmem) != cudaSuccess)
+      g_have_tc = false;
+  for (const void* k : k2)
+    if (g_have_tc && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Stages<2>::kSmem) != cudaSuccess)
       g_have_tc = false;
 }
 
@@ -546,15 +590,34 @@ cudaError_t launch_gemm_tc_bf16(const GemmArgs<bf16>& a, cudaStream_t st) {
   }
   dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM);
   const int two = a.Bm2 ? 1 : 0;
+  if (a.op < 0 || a.op >= kNumOps) return cudaErrorInvalidValue;
+  // K chunks per stage: the chunked views cover the floor(K / 64) whole
+  // chunks (the partial last chunk goes through the 2D maps' zero fill)
+  const int kfull = a.K / BK;
+  const int kc = kfull >= 2 ? kStageChunks[a.op] : 1;
+  CUtensorMap mac = ma, mbc = mb, mb2c = mb2;
+  if (kc == 2 && (!tc_encode_bf16_chunks(&mac, a.A, a.M, kfull * BK, a.lda, BM, 2) ||
+                  !tc_encode_bf16_chunks(&mbc, a.Bm, a.N, kfull * BK, a.ldb, BN, 2) ||
+                  (a.Bm2 && !tc_encode_bf16_chunks(&mb2c, a.Bm2, a.N, kfull * BK, a.ldb, BN, 2))))
+    return cudaErrorInvalidValue;
+  if (kc == 2 && !a.Bm2) mb2c = mbc;
+#define VQMC_GEMM_LAUNCH(OP)                                                                                   \
+  case OP:                                                                                                     \
+    if (kc == 2)                                                                                               \
+      gemm_tc_kernel<OP, 2><<<grid, kThreads, Stages<2>::kSmem, st>>>(ma, mb, mb2, mac, mbc, mb2c, a, two, kfull); \
+    else                                                                                                       \
+      gemm_tc_kernel<OP, 1><<<grid, kThreads, Stages<1>::kSmem, st>>>(ma, mb, mb2, mac, mbc, mb2c, a, two, kfull); \
+    break;
   switch (a.op) {
-    case kOpHidden: gemm_tc_kernel<kOpHidden><<<grid, kThreads, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
-    case kOpOut: gemm_tc_kernel<kOpOut><<<grid, kThreads, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
-    case kOpDV: gemm_tc_kernel<kOpDV><<<grid, kThreads, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
-    case kOpGA: gemm_tc_kernel<kOpGA><<<grid, kThreads, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
-    case kOpDW: gemm_tc_kernel<kOpDW><<<grid, kThreads, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
-    case kOpEloc: gemm_tc_kernel<kOpEloc><<<grid, kThreads, SMEM_BYTES, st>>>(ma, mb, mb2, a, two); break;
+    VQMC_GEMM_LAUNCH(kOpHidden)
+    VQMC_GEMM_LAUNCH(kOpOut)
+    VQMC_GEMM_LAUNCH(kOpDV)
+    VQMC_GEMM_LAUNCH(kOpGA)
+    VQMC_GEMM_LAUNCH(kOpDW)
+    VQMC_GEMM_LAUNCH(kOpEloc)
     default: return cudaErrorInvalidValue;
   }
+#undef VQMC_GEMM_LAUNCH
   return cudaGetLastError();
 }
 
