@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int cnt = min(kSlotTiles, i1 - i);
           const int s = it % kNSlot;
           if (it >= kNSlot &&
-              !wait_or_abort(smem_u32(&empty[s]), (uint32_t)((it / kNSlot - 1) & 1), abort, g.err, true))
+              !wait_or_abort(smem_u32(&empty[s]), (uint32_t)((it / kNSlot - 1) & 1), abort, g.err))
             return false;
           const uint32_t bar = smem_u32(&full[s]);
           mbar_expect_tx(bar, (uint32_t)(cnt * kTileBytes));
@@ -612,36 +612,66 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     };
-    // spins of block b (bits in SB buffer b & 1) to the output; threads t0, t0 + nt, ...
+    // spins of block b (bits in SB buffer b & 1) to the outputs; threads t0,
+    // t0 + nt, ...  Runs of 16 steps of one sample (s_out, sx) and the 16
+    // samples of one step (stt) go out as 16-byte stores where the whole run
+    // is inside the output and aligned, else element by element.
     auto write_spins = [&](int b, int t0, int nt) {
       const uint32_t* sb = SB + (b & 1) * kS * (kDmax / 32);
       const int steps = min(D, n - b * D);
       const bf16 one = __float2bfloat16_rn(1.0f), mone = __float2bfloat16_rn(-1.0f);
-      for (int q = t0; q < kS * D; q += nt) {
-        const int s = q / D, e = q % D;
+      // two spins as BF16 (+1 = 0x3F80, -1 = 0xBF80); bit set in dn: spin -1
+      auto bf_pair = [](uint32_t dn) { return 0x3F803F80u | (dn & 1u) << 15 | (dn >> 1 & 1u) << 31; };
+      for (int q = t0; q < kS * (kDmax / 16); q += nt) {
+        const int s = q / (kDmax / 16), e0 = 16 * (q % (kDmax / 16));
         const int bb = b0 + s;
-        if (bb < g.B && e < steps) {
-          const bool up = (sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u;
-          g.s_out[(size_t)bb * n + b * D + e] = up ? (int8_t)1 : (int8_t)-1;
-          if (g.sx) g.sx[(size_t)bb * g.ldsx + b * D + e] = up ? one : mone;
+        if (bb >= g.B || e0 >= steps) continue;
+        const uint32_t up = (sb[s * (kDmax / 32) + (e0 >> 5)] >> (e0 & 16)) & 0xFFFFu;  // bit k: step e0 + k is +1
+        const int cnt = min(16, steps - e0);
+        int8_t* so = g.s_out + (size_t)bb * n + b * D + e0;
+        if (cnt == 16 && (reinterpret_cast<uintptr_t>(so) & 15) == 0) {
+          uint32_t w[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            // the 4 bits spread to bit 0 of 4 bytes (the shifted copies do
+            // not overlap), then +1 -> 0x01 and -1 -> 0xFF per byte
+            const uint32_t m = ((up >> (4 * p)) & 0xFu) * 0x00204081u & 0x01010101u;
+            w[p] = m | (m ^ 0x01010101u) * 0xFFu;
+          }
+          *reinterpret_cast<uint4*>(so) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+          for (int k = 0; k < cnt; ++k) so[k] = (up >> k) & 1u ? (int8_t)1 : (int8_t)-1;
         }
-      }
-      if (g.stt)
-        for (int q = t0; q < kS * D; q += nt) {
-          const int e = q / kS, s = q % kS;
-          const int bb = b0 + s;
-          if (bb < g.B && e < steps) {
-            const bool up = (sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u;
-            g.stt[(size_t)(b * D + e) * g.ldst + bb] = up ? one : mone;
+        if (g.sx) {
+          bf16* dx = g.sx + (size_t)bb * g.ldsx + b * D + e0;
+          if (cnt == 16 && (reinterpret_cast<uintptr_t>(dx) & 15) == 0) {
+            const uint32_t dn = ~up;
+            uint4* d4 = reinterpret_cast<uint4*>(dx);
+            d4[0] = make_uint4(bf_pair(dn), bf_pair(dn >> 2), bf_pair(dn >> 4), bf_pair(dn >> 6));
+            d4[1] = make_uint4(bf_pair(dn >> 8), bf_pair(dn >> 10), bf_pair(dn >> 12), bf_pair(dn >> 14));
+          } else {
+            for (int k = 0; k < cnt; ++k) dx[k] = (up >> k) & 1u ? one : mone;
           }
         }
-      if (g.sbits)
+      }
+      if (g.stt || g.sbits)
         for (int e = t0; e < steps; e += nt) {
-          uint32_t w = 0;
+          uint32_t dn = 0;  // bit s: sample b0 + s has spin -1 at step e
 #pragma unroll
           for (int s = 0; s < kS; ++s)
-            if (b0 + s < g.B && !((sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u)) w |= 1u << s;
-          g.sbits[((size_t)(b0 >> 5) * n + b * D + e) * 2 + ((b0 >> 4) & 1)] = (uint16_t)w;
+            if (b0 + s < g.B && !((sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u)) dn |= 1u << s;
+          if (g.stt) {
+            bf16* dt = g.stt + (size_t)(b * D + e) * g.ldst + b0;
+            if (b0 + kS <= g.B && (reinterpret_cast<uintptr_t>(dt) & 15) == 0) {
+              uint4* d4 = reinterpret_cast<uint4*>(dt);
+              d4[0] = make_uint4(bf_pair(dn), bf_pair(dn >> 2), bf_pair(dn >> 4), bf_pair(dn >> 6));
+              d4[1] = make_uint4(bf_pair(dn >> 8), bf_pair(dn >> 10), bf_pair(dn >> 12), bf_pair(dn >> 14));
+            } else {
+              for (int s = 0; s < kS; ++s)
+                if (b0 + s < g.B) dt[s] = (dn >> s) & 1u ? mone : one;
+            }
+          }
+          if (g.sbits) g.sbits[((size_t)(b0 >> 5) * n + b * D + e) * 2 + ((b0 >> 4) & 1)] = (uint16_t)dn;
         }
     };
     // The recent units' weights of block bb (W2 rows of its steps, W1 of its
