@@ -158,6 +158,7 @@ struct vqmc_ctx {
   int32_t* eloc_slice = nullptr;  // [eloc_slices + 1] first CSR row of each slice
   int32_t* erow = nullptr;        // [nnz] CSR row of each edge
   int eloc_slices = 1;
+  int eloc_wbits = 32;            // bit length of the largest |J_ij| (int32 instances)
   void* E = nullptr;       // int32/float [Bmax]
   void* Sx = nullptr;      // [Bmax][np] spins as GEMM operand
   void* St = nullptr;      // [n][Bp] spins transposed

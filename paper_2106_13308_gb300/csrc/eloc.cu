@@ -105,6 +105,114 @@ __global__ void __launch_bounds__(kElocWarps * 32) eloc_sparse_kernel(int B, int
   }
 }
 
+// Bit-sliced variant for small integer weights (|J_ij| < 2^(PL - 5)): the
+// lanes take different edges and each handles all 32 samples of the word at
+// once.  With x = bit_i xor bit_j (bit set: s_i s_j = -1), the slice's part
+// of E_b is W - 2 sum_e J_e x_{e,b}, W the slice's weight sum.  A lane adds
+// J_e x_e into a two's-complement counter kept as bit planes (bit b of plane
+// t: bit t of sample b's partial sum; each addition a ripple of full adders
+// over the planes): PL planes for runs of 15 edges (15 (2^(PL-5) - 1) <
+// 2^(PL-1)), each run then sign-extended into 32 planes.  The lanes' and then
+// the warps' counters are added plane-wise in a fixed order, and lane b
+// finally reads sample b's integer off the planes.  The result equals the
+// plain kernel's bit for bit (both are W - 2 sum J x in int32).
+__device__ __forceinline__ void add_planes32(uint32_t (&C)[32], const uint32_t (&a)[32]) {
+  uint32_t c = 0;
+#pragma unroll
+  for (int t = 0; t < 32; ++t) {
+    const uint32_t s = C[t] ^ a[t] ^ c;
+    c = (C[t] & a[t]) | (c & (C[t] ^ a[t]));
+    C[t] = s;
+  }
+}
+
+template <int PL>
+__global__ void __launch_bounds__(kElocWarps * 32) eloc_sliced_kernel(int B, int n, const uint32_t* __restrict__ Sbits,
+                                                                     const int32_t* __restrict__ row_ptr,
+                                                                     const int32_t* __restrict__ erow,
+                                                                     const int32_t* __restrict__ col,
+                                                                     const int32_t* __restrict__ w,
+                                                                     const int32_t* __restrict__ field,
+                                                                     const int32_t* __restrict__ slice,
+                                                                     int32_t* __restrict__ part, int ldp) {
+  extern __shared__ uint32_t bits[];  // [n]
+  __shared__ uint32_t planes[kElocWarps][32];
+  __shared__ int32_t fpart[kElocWarps][32];
+  __shared__ int32_t wpart[kElocWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wd = blockIdx.x, q = blockIdx.y;
+  const uint32_t* src = Sbits + (size_t)wd * n;
+  for (int i = threadIdx.x; i < n; i += kElocWarps * 32) bits[i] = __ldg(src + i);
+  __syncthreads();
+  const int r0 = __ldg(slice + q), r1 = __ldg(slice + q + 1);
+  // the field: lane = sample, as in the plain kernel
+  int32_t fe = 0;
+  if (field)
+    for (int i = r0 + warp; i < r1; i += kElocWarps) {
+      const int32_t f = __ldg(field + i);
+      fe += ((bits[i] >> lane) & 1u) ? -f : f;
+    }
+  const int pa = __ldg(row_ptr + r0), pb = __ldg(row_ptr + r1);
+  uint32_t C[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) C[t] = 0u;
+  int32_t ws = 0;
+  for (int p = pa + (int)threadIdx.x; p < pb;) {
+    uint32_t L[PL];
+#pragma unroll
+    for (int t = 0; t < PL; ++t) L[t] = 0u;
+    for (int k = 0; k < 15 && p < pb; ++k, p += kElocWarps * 32) {
+      const int32_t wt = __ldg(w + p);
+      const uint32_t x = bits[__ldg(erow + p)] ^ bits[__ldg(col + p)];
+      ws += wt;
+      uint32_t c = 0;
+#pragma unroll
+      for (int t = 0; t < PL; ++t) {
+        const uint32_t a = ((uint32_t)wt >> t) & 1u ? x : 0u;  // plane t of wt x (two's complement)
+        const uint32_t sum = L[t] ^ a ^ c;
+        c = (L[t] & a) | (c & (L[t] ^ a));
+        L[t] = sum;
+      }
+    }
+    uint32_t a[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) a[t] = L[t < PL ? t : PL - 1];  // sign extension
+    add_planes32(C, a);
+  }
+  // the warp's lanes, then the CTA's warps (fixed order)
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t o[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) o[t] = __shfl_xor_sync(0xffffffffu, C[t], d);
+    add_planes32(C, o);
+    ws += __shfl_xor_sync(0xffffffffu, ws, d);
+  }
+  planes[warp][lane] = C[lane];
+  fpart[warp][lane] = fe;
+  if (lane == 0) wpart[warp] = ws;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t T[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) T[t] = planes[0][t];
+    int32_t wsum = wpart[0], f = fpart[0][lane];
+    for (int k = 1; k < kElocWarps; ++k) {
+      uint32_t o[32];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) o[t] = planes[k][t];
+      add_planes32(T, o);
+      wsum += wpart[k];
+      f += fpart[k][lane];
+    }
+    uint32_t v = 0;  // sample lane's sum of J x (two's complement)
+#pragma unroll
+    for (int t = 0; t < 32; ++t) v |= ((T[t] >> lane) & 1u) << t;
+    const int b = 32 * wd + lane;
+    if (b < B) part[(size_t)q * ldp + b] = (int32_t)((uint32_t)wsum - 2u * v) + f;
+  }
+}
+
 // E_b = sum of the slices' partial energies, in slice order
 template <typename A>
 __global__ void eloc_sum_kernel(int B, int nslices, const A* __restrict__ part, int ldp, A* __restrict__ E) {
@@ -231,6 +339,21 @@ __global__ void tile_sum_kernel(int cnt, int ntiles, const float* __restrict__ p
 
 }  // namespace
 
+template <int PL>
+cudaError_t eloc_sliced(const vqmc_ctx* c, int B, void* d_e, cudaStream_t st) {
+  const size_t smem = (size_t)c->n * sizeof(uint32_t);
+  auto k = eloc_sliced_kernel<PL>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int ns = c->eloc_slices;
+  int32_t* part = ns > 1 ? (int32_t*)c->eloc_part : (int32_t*)d_e;
+  k<<<dim3((B + 31) / 32, ns), kElocWarps * 32, smem, st>>>(B, c->n, c->Sbits, c->row_ptr, c->erow, c->col,
+                                                           (const int32_t*)c->w, (const int32_t*)c->field,
+                                                           c->eloc_slice, part, c->Bmax);
+  if (ns > 1) eloc_sum_kernel<int32_t><<<(B + 255) / 256, 256, 0, st>>>(B, ns, part, c->Bmax, (int32_t*)d_e);
+  return cudaGetLastError();
+}
+
 template <typename W, typename A>
 cudaError_t eloc_sparse(const vqmc_ctx* c, int B, void* d_e, cudaStream_t st) {
   const size_t smem = (size_t)c->n * sizeof(uint32_t);
@@ -250,8 +373,14 @@ cudaError_t launch_eloc_sparse(const vqmc_ctx* c, int B, const int8_t* d_s, void
                                bool packed) {
   if (B <= 0) return cudaSuccess;
   if (!packed) pack_bits_kernel<<<dim3((c->n + 255) / 256, (B + 31) / 32), 256, 0, st>>>(B, c->n, d_s, c->Sbits);
-  return c->ham == VQMC_HAM_SPARSE_I32 ? eloc_sparse<int32_t, int32_t>(c, B, d_e, st)
-                                       : eloc_sparse<float, float>(c, B, d_e, st);
+  if (c->ham == VQMC_HAM_SPARSE_I32) {
+    // weights of at most 8 bits (magnitude): the bit-sliced kernel
+    if (c->eloc_wbits <= 1) return eloc_sliced<6>(c, B, d_e, st);
+    if (c->eloc_wbits <= 4) return eloc_sliced<9>(c, B, d_e, st);
+    if (c->eloc_wbits <= 8) return eloc_sliced<13>(c, B, d_e, st);
+    return eloc_sparse<int32_t, int32_t>(c, B, d_e, st);
+  }
+  return eloc_sparse<float, float>(c, B, d_e, st);
 }
 
 cudaError_t launch_eloc_dense_finish(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st) {

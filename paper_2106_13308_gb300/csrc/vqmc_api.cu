@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -355,6 +356,16 @@ vqmc_status vqmc_create(const vqmc_config* cfg, const vqmc_instance* inst, vqmc_
       rb[q] = i;
     }
     c->eloc_slices = slices;
+    if (c->ham == VQMC_HAM_SPARSE_I32) {
+      long long wmax = 0;  // the bit-sliced energy kernel needs |J_ij| < 2^wbits
+      for (long long p = 0; p < c->nnz; ++p) {
+        const long long a = std::llabs((long long)((const int32_t*)inst->w)[p]);
+        wmax = a > wmax ? a : wmax;
+      }
+      int wb = 0;
+      while (wb < 32 && (1ll << wb) <= wmax) ++wb;
+      c->eloc_wbits = wb;
+    }
     std::vector<int32_t> er((size_t)c->nnz);
     for (int i = 0; i < n; ++i)
       for (int p = inst->row_ptr[i]; p < inst->row_ptr[i + 1]; ++p) er[(size_t)p] = i;

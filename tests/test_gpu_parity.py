@@ -208,6 +208,23 @@ def test_sparse_energy_bit_exact():
         assert np.array_equal((inst["w"].sum() - E) // 2, oracle.cut(inst, S).astype(np.int64))
 
 
+@pytest.mark.parametrize("lo,hi", [(-1, 1), (0, 0), (-15, 15), (1, 10), (-255, 255), (-256, 256), (-70000, 70000)])
+def test_sparse_energy_weight_widths(lo, hi):
+    """Integer weights of every width the energy kernels distinguish (|J| < 2,
+    16, 256: bit-sliced counters of 6, 9 or 13 planes; wider: one sample per
+    lane), on rows long enough that each thread adds many runs of 15 edges
+    (n = 2000, p = 0.1: about 2e5 edges, 10 row slices for B = 1024) and a
+    ragged last word of samples: bit-exact against the oracle."""
+    n, B = 2000, 1000
+    e = inputs.erdos_renyi(n, 0.1, 41)
+    inst = inputs.to_csr(n, e, inputs.int_weights(len(e), lo, hi, 42))
+    m = make_model(n, 8, 1024, inst)
+    S = inputs.spins(B, n, 43)
+    E = m.local_energy(torch.from_numpy(S).cuda()).cpu().numpy()
+    assert E.dtype == np.int32 and np.array_equal(E.astype(np.float64), oracle.energy(inst, S))
+    m.close()
+
+
 def test_sparse_energy_with_field_and_pm1_weights():
     n, B = 1000, 130
     e = inputs.random_regular(n, 3, 21)
