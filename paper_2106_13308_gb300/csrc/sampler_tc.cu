@@ -35,6 +35,7 @@
 // lane 0 issues the MMAs.  Every wait is bounded; after a failed wait the CTA
 // raises the timeout bit and runs on without waiting, so it still finishes.
 #include <algorithm>
+#include <type_traits>
 
 #include "gemm.cuh"
 #include "sampler.cuh"
@@ -196,14 +197,22 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
   reinterpret_cast<float4*>(hh)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncwarp();
   uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;  // this lane's drawn spins: bit e % 32 of word e / 32
-  // Z_e + b2 + the terms of the recent units completed so far (hh)
-  auto zdot = [&](int e) -> float {
+  // The segments run in four phases by r / 8 (a template parameter PH of the
+  // helpers below): in segment r only units 0 .. r-1 are complete (g1 != 0
+  // in hh) and only units r .. 31 still need partial sums, so the logit's dot
+  // product reads the 8-unit chunks 0 .. PH, the weight-row update writes the
+  // chunks PH .. 3 and the completing unit's partial sum is one of 16.  The
+  // skipped terms are zeros (g1 of incomplete units) or sums never read
+  // again, so the draws are those of the full loops.
+  // Z_e + b2 + the terms of the recent units completed so far (hh, chunks 0 .. PH)
+  auto zdot = [&](auto ph, int e) -> float {
+    constexpr int PH = decltype(ph)::value;
     const uint4* vr = reinterpret_cast<const uint4*>(Vr + e * kLdW);
     const float4* hv = reinterpret_cast<const float4*>(hh);
     // four FP32 accumulators a0..a3 as the pairs (a0, a1), (a2, a3)
     uint64_t a01 = pk2(Zs[e * kZld + s_me], 0.0f), a23 = pk2(0.0f, 0.0f);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c <= PH; ++c) {
       const uint4 v = vr[c];
       const float4 x = hv[2 * c], y = hv[2 * c + 1];
       a01 = fma2(bf2(v.x), pk2(x.x, x.y), a01);
@@ -216,12 +225,13 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
     upk2(a23, a2, a3);
     return (a0 + a1) + (a2 + a3);
   };
-  // this lane's partial sums of all recent units += sv * W1 of step row el
-  auto wrow = [&](int el, float sv) {
+  // this lane's partial sums of the recent units of chunks PH .. 3 += sv * W1 of step row el
+  auto wrow = [&](auto ph, int el, float sv) {
+    constexpr int PH = decltype(ph)::value;
     const uint4* wr = reinterpret_cast<const uint4*>(Wr + el * kLdW);
     const uint64_t s2 = pk2(sv, sv);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = PH; c < 4; ++c) {
       const uint4 w = wr[c];
       const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -233,7 +243,7 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
     }
   };
   // draw of step e from its logit, and the spin into this lane's partial sums
-  auto draw = [&](int e, float z) {
+  auto draw = [&](auto ph, int e, float z) {
     const bool up = z > LG[e * kS + s_me];  // u < sigma(z)
     const uint32_t m = up ? 1u << (e & 31) : 0u;
     const int wd = e >> 5;
@@ -242,20 +252,23 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
     w2 |= wd == 2 ? m : 0u;
     w3 |= wd == 3 ? m : 0u;
     if constexpr (LP) lp += log_sigmoid(up ? z : -z);
-    wrow(e, up ? 1.0f : -1.0f);
+    wrow(ph, e, up ? 1.0f : -1.0f);
   };
-  // the partial sum of unit r among this lane's 32 (a binary select by r)
-  auto extract = [&](int r) -> float {
-    float l1[16], l2[8], l3[4], l4[2];
+  // the partial sum of unit k among this lane's units 8 PH .. 8 PH + 15
+  // (8 PH .. 31 in the last phase): a binary select by k - 8 PH
+  auto extract = [&](auto ph, int k) -> float {
+    constexpr int PH = decltype(ph)::value;
+    constexpr int kB = 8 * PH, kN = PH < 3 ? 16 : 8;
+    const int i = k - kB;
+    float l1[kN / 2], l2[kN / 4], l3[kN / 8];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) l1[k] = (r & 1) ? P[2 * k + 1] : P[2 * k];
+    for (int t = 0; t < kN / 2; ++t) l1[t] = (i & 1) ? P[kB + 2 * t + 1] : P[kB + 2 * t];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) l2[k] = (r & 2) ? l1[2 * k + 1] : l1[2 * k];
+    for (int t = 0; t < kN / 4; ++t) l2[t] = (i & 2) ? l1[2 * t + 1] : l1[2 * t];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) l3[k] = (r & 4) ? l2[2 * k + 1] : l2[2 * k];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) l4[k] = (r & 8) ? l3[2 * k + 1] : l3[2 * k];
-    return (r & 16) ? l4[1] : l4[0];
+    for (int t = 0; t < kN / 8; ++t) l3[t] = (i & 4) ? l2[2 * t + 1] : l2[2 * t];
+    if constexpr (kN == 16) return (i & 8) ? l3[1] : l3[0];
+    else return l3[0];
   };
   auto wt = [&](int e, int r) { return r < kRmax ? __bfloat162float(Wr[e * kLdW + r]) : 0.0f; };
   auto vt = [&](int e, int r) { return r >= 0 ? __bfloat162float(Vr[e * kLdW + r]) : 0.0f; };
@@ -274,14 +287,16 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
   // without a step in the segment (e past its end) draws nothing (sv = 0)
   // and reads row min(e, kDrows - 1) of the tables, so that the compiler can
   // move the next segment's loads ahead of the completion chain.
+  using Ph0 = std::integral_constant<int, 0>;
   float g_last = 0.0f;  // g1 of the unit that completed last
   int lo = 0;
   int e = q;
   int hi = R > 0 ? TC[0] : steps - 1;  // last step of the current segment
   float zp = 0.0f, vn = 0.0f, lgn = 0.0f, wn = 0.0f, xr = 0.0f;
-  if (e <= hi) zp = zdot(e), lgn = LG[e * kS + s_me], wn = wt(e, 0);
-  xr = extract(0);
-  for (int r = 0; r <= R; ++r) {  // segment r: steps [lo, hi], units 0 .. r-1 complete
+  if (e <= hi) zp = zdot(Ph0{}, e), lgn = LG[e * kS + s_me], wn = wt(e, 0);
+  xr = extract(Ph0{}, 0);
+  // segment r: steps [lo, hi], units 0 .. r-1 complete; true after the last (r = R)
+  auto segment = [&](auto ph, int r) -> bool {
     const int nhi = r + 1 < R ? TC[r + 1] : steps - 1;  // last step of segment r + 1
     hh[r > 0 ? r - 1 : 0] = g_last;                     // (unit 0's entry is still zero at r = 0)
     float x;
@@ -300,30 +315,37 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
       w2 |= wd == 2 ? m : 0u;
       w3 |= wd == 3 ? m : 0u;
       if constexpr (LP) lp += own ? log_sigmoid(up ? z : -z) : 0.0f;
-      wrow(el, sv);
+      wrow(ph, el, sv);
     } else {
       // ---- a long segment: every step of the lane with its full logit,
       // then unit r's partial sums
-      for (int ee = lo + ((q - lo) & (kLanes - 1)); ee <= hi; ee += kLanes) draw(ee, zdot(ee));
-      x = allsum(extract(r));
+      for (int ee = lo + ((q - lo) & (kLanes - 1)); ee <= hi; ee += kLanes) draw(ph, ee, zdot(ph, ee));
+      x = allsum(extract(ph, r < kRmax ? r : kRmax - 1));
     }
-    if (r == R) break;
+    if (r == R) return true;
     // prepare this lane's step of segment r + 1 (hh holds units 0 .. r-1);
     // a lane without one (e > nhi) keeps values that its sv = 0 ignores
     const int nlo = hi + 1;
     e = nlo + ((q - nlo) & (kLanes - 1));
     {
       const int el = min(e, kDrows - 1);
-      zp = zdot(el);
+      zp = zdot(ph, el);
       vn = vt(el, r);
       lgn = LG[el * kS + s_me];
       wn = wt(el, r + 1);
     }
-    xr = extract(r + 1 < kRmax ? r + 1 : kRmax - 1);
+    xr = extract(ph, r + 1 < kRmax ? r + 1 : kRmax - 1);
     g_last = bf16r(g1f<ACT>(x));
     lo = nlo;
     hi = nhi;
-  }
+    return false;
+  };
+  bool last = false;
+  int r = 0;
+  for (; r < 8 && !last; ++r) last = segment(Ph0{}, r);
+  for (; r < 16 && !last; ++r) last = segment(std::integral_constant<int, 1>{}, r);
+  for (; r < 24 && !last; ++r) last = segment(std::integral_constant<int, 2>{}, r);
+  for (; !last; ++r) last = segment(std::integral_constant<int, 3>{}, r);  // r <= R <= 32
   // the sample's spins: its lanes' words combined; lane q < 4 stores word q
 #pragma unroll
   for (int d = 1; d < kLanes; d <<= 1) {
