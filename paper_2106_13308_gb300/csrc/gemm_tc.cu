@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, Stages<KC>::kMinBlocks)
     // --------------------------------------------------------- MMA issuer
     for (int it = 0; it < nkt && ok; ++it) {
       const int s = it % NSTAGE;
-      ok = mbar_wait(smem_u32(&full[s]), (uint32_t)((it / NSTAGE) & 1), err);
+      ok = mbar_poll(smem_u32(&full[s]), (uint32_t)((it / NSTAGE) & 1), err);
       if (!ok) break;
       fence_after();
       const int pass = it / per_pass, kt = kt0 + KC * (it - pass * per_pass);

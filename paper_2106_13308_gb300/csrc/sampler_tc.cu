@@ -145,6 +145,18 @@ __device__ __forceinline__ uint64_t bf2(uint32_t w) { return pk2(bf_lo(w), bf_hi
 // bounded wait that gives up at once after any failure in the CTA; with
 // backoff the polling thread sleeps between tries so that it takes no issue
 // slots from a busy warp on the same sub-partition
+// The same wait polling with mbarrier.test_wait, which returns at once: for
+// the MMA issuer's waits on landed tiles, which are usually already complete
+// (a try_wait there costs the issuing thread about 190 cycles even then).
+__device__ __forceinline__ bool test_or_abort(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t* err) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    if (mbar_test_wait(bar, parity)) return true;
+    if ((it & 255) == 255 && *abort) return false;
+  }
+  atomicOr(err, kErrTimeout);
+  *abort = 1;
+  return false;
+}
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t* err,
                                               bool backoff = false) {
   if (*abort) return false;
@@ -548,7 +560,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = i0; i < i1; i += kSlotTiles) {
           const int cnt = min(kSlotTiles, i1 - i);
           const int s = it % kNSlot;
-          if (!wait_or_abort(smem_u32(&full[s]), (uint32_t)((it / kNSlot) & 1), abort, g.err)) return false;
+          if (!test_or_abort(smem_u32(&full[s]), (uint32_t)((it / kNSlot) & 1), abort, g.err)) return false;
           fence_after();
           for (int j = 0; j < cnt; ++j) {
             uint32_t dcol, bop;

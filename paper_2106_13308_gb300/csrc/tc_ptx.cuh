@@ -39,6 +39,26 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_
   if (err) atomicOr(err, kErrTimeout);
   return false;
 }
+// Non-blocking probe of a phase (returns at once).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait by test_wait polling, for waits that are usually already
+// satisfied (the MMA issuer on landed operand stages).
+__device__ __forceinline__ bool mbar_poll(uint32_t bar, uint32_t parity, uint32_t* err) {
+  for (long long it = 0; it < kSpinLimit; ++it)
+    if (mbar_test_wait(bar, parity)) return true;
+  if (err) atomicOr(err, kErrTimeout);
+  return false;
+}
 
 // 2D tiled TMA load of the box at (x = inner element, y = row), completing
 // transaction bytes on bar.  Callers pass x as a multiple of 64 elements.
