@@ -240,24 +240,51 @@ __global__ void eloc_dense_finish_kernel(int B, int n, int ntiles, const float* 
 
 // FP64 statistics of B energies in one CTA with a fixed reduction order.
 // With ds set, thread 0 also starts the next Adam step (t += 1 and its bias
-// corrections), which the gradient kernels after it read.
+// corrections), which the gradient kernels after it read.  FP64 arithmetic
+// is slow on this part, so integer energies are summed in int64 and their
+// extremes taken in int32 (exact: the same mean as an FP64 sum, whose
+// partial sums are exact integers), and the coefficients (E_b - mean) / B
+// multiply by 1 / B (exact for B a power of two; otherwise within one
+// rounding of the quotient before the conversion to FP32).
+template <typename A>
+struct StatAcc;
+template <>
+struct StatAcc<int32_t> {
+  using S = long long;
+  using M = int32_t;
+  static __device__ __forceinline__ M lo() { return 0x7fffffff; }
+  static __device__ __forceinline__ M hi() { return -0x7fffffff - 1; }
+};
+template <>
+struct StatAcc<float> {
+  using S = double;
+  using M = double;
+  static __device__ __forceinline__ M lo() { return 1.0 / 0.0; }
+  static __device__ __forceinline__ M hi() { return -1.0 / 0.0; }
+};
+
 template <typename A>
 __global__ void __launch_bounds__(1024) stats_kernel(int B, const A* __restrict__ E, double* __restrict__ out,
                                                      float* __restrict__ coef, uint32_t* __restrict__ err,
                                                      DevState* ds, float beta1, float beta2) {
-  __shared__ double s_sum[1024], s_min[1024], s_max[1024];
+  using S = typename StatAcc<A>::S;
+  using M = typename StatAcc<A>::M;
+  __shared__ S s_sum[1024];
+  __shared__ M s_min[1024], s_max[1024];
+  __shared__ double s_var[1024];
   __shared__ double s_mean;
   const int t = threadIdx.x;
   if (ds && t == 0) {
     ds->adam_t += 1;
     adam_factors(ds, beta1, beta2);
   }
-  double sum = 0.0, mn = 1.0 / 0.0, mx = -1.0 / 0.0;
+  S sum = 0;
+  M mn = StatAcc<A>::lo(), mx = StatAcc<A>::hi();
   for (int b = t; b < B; b += 1024) {
-    const double x = (double)E[b];
-    sum += x;
-    mn = fmin(mn, x);
-    mx = fmax(mx, x);
+    const A x = E[b];
+    sum += (S)x;
+    mn = (M)x < mn ? (M)x : mn;
+    mx = (M)x > mx ? (M)x : mx;
   }
   s_sum[t] = sum;
   s_min[t] = mn;
@@ -266,12 +293,12 @@ __global__ void __launch_bounds__(1024) stats_kernel(int B, const A* __restrict_
   for (int o = 512; o > 0; o >>= 1) {
     if (t < o) {
       s_sum[t] += s_sum[t + o];
-      s_min[t] = fmin(s_min[t], s_min[t + o]);
-      s_max[t] = fmax(s_max[t], s_max[t + o]);
+      s_min[t] = s_min[t + o] < s_min[t] ? s_min[t + o] : s_min[t];
+      s_max[t] = s_max[t + o] > s_max[t] ? s_max[t + o] : s_max[t];
     }
     __syncthreads();
   }
-  if (t == 0) s_mean = s_sum[0] / (double)B;
+  if (t == 0) s_mean = (double)s_sum[0] / (double)B;
   __syncthreads();
   const double mean = s_mean;
   double ss = 0.0;
@@ -279,23 +306,24 @@ __global__ void __launch_bounds__(1024) stats_kernel(int B, const A* __restrict_
     const double d = (double)E[b] - mean;
     ss += d * d;
   }
-  __syncthreads();
-  s_sum[t] = ss;
+  s_var[t] = ss;
   __syncthreads();
   for (int o = 512; o > 0; o >>= 1) {
-    if (t < o) s_sum[t] += s_sum[t + o];
+    if (t < o) s_var[t] += s_var[t + o];
     __syncthreads();
   }
   if (t == 0) {
-    const double var = s_sum[0] / (double)B;
+    const double var = s_var[0] / (double)B;
     out[0] = mean;
     out[1] = var;
-    out[2] = s_min[0];
-    out[3] = s_max[0];
+    out[2] = (double)s_min[0];
+    out[3] = (double)s_max[0];
     if (!isfinite(mean) || !isfinite(var)) atomicOr(err, kErrNonfinite);
   }
-  if (coef)
-    for (int b = t; b < B; b += 1024) coef[b] = (float)(((double)E[b] - mean) / (double)B);
+  if (coef) {
+    const double inv = 1.0 / (double)B;
+    for (int b = t; b < B; b += 1024) coef[b] = (float)(((double)E[b] - mean) * inv);
+  }
 }
 
 template <typename T>

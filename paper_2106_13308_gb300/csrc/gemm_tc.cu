@@ -249,7 +249,16 @@ __global__ void __launch_bounds__(kThreads, Stages<KC>::kMinBlocks)
   constexpr int op = OP;
   constexpr bool kWgrad = op == kOpDV || op == kOpDW;
   const bool fused = kWgrad && g.theta != nullptr;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  // Tiles in launch order, heaviest K range first where the masks make the
+  // ranges uneven (the hidden GEMM: K grows with the N-tile; the hidden
+  // adjoint: K shrinks with it), so that the last wave holds the light tiles.
+  int tm = blockIdx.y, tn = blockIdx.x;
+  if constexpr (OP == kOpHidden || OP == kOpGA) {
+    const int L = blockIdx.y * gridDim.x + blockIdx.x;  // launch order
+    tm = L % gridDim.y;
+    tn = OP == kOpHidden ? (int)gridDim.x - 1 - L / (int)gridDim.y : L / (int)gridDim.y;
+  }
+  const int m0 = tm * BM, n0 = tn * BN;
   const int m1 = min(m0 + BM, g.M), n1 = min(n0 + BN, g.N);
 
   // fully masked weight-gradient tiles: zeros (or, with the fused Adam step, nothing)
@@ -495,10 +504,10 @@ __global__ void __launch_bounds__(kThreads, Stages<KC>::kMinBlocks)
   fence_before();
   __syncthreads();
   if (kRows && half == 0 && g.row_part && mvalid)
-    g.row_part[(size_t)blockIdx.x * g.ldr + m] = rowsum + rowbuf[quad * 32 + lane];
+    g.row_part[(size_t)tn * g.ldr + m] = rowsum + rowbuf[quad * 32 + lane];
   if (want_col && tid < BN && n0 + tid < g.N) {
     const float v = colbuf[tid] + colbuf[BN + tid] + colbuf[2 * BN + tid] + colbuf[3 * BN + tid];
-    g.col_part[(size_t)blockIdx.y * g.ldc + n0 + tid] = v;
+    g.col_part[(size_t)tm * g.ldc + n0 + tid] = v;
   }
   if (warp == 0) {
     fence_after();
