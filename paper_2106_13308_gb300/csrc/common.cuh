@@ -221,7 +221,7 @@ cudaError_t launch_sampler_tc(const vqmc_ctx* c, int B, const float* d_u, uint64
 // ---- eloc.cu
 // packed: c->Sbits already holds the spins (written by the sampler)
 cudaError_t launch_eloc_sparse(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st,
-                               bool packed = false);
+                               bool packed = false, bool beside = false);
 cudaError_t launch_eloc_dense_finish(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st);
 // ---- tim.cu: adds the transverse field's off-diagonal local energy to d_e
 // (float [B]); *launches (if not null) receives the number of kernels

@@ -126,7 +126,7 @@ __device__ __forceinline__ void add_planes32(uint32_t (&C)[32], const uint32_t (
   }
 }
 
-template <int PL>
+template <int PL, bool STAGE>
 __global__ void __launch_bounds__(kElocWarps * 32) eloc_sliced_kernel(int B, int n, const uint32_t* __restrict__ Sbits,
                                                                      const int32_t* __restrict__ row_ptr,
                                                                      const int32_t* __restrict__ erow,
@@ -135,22 +135,30 @@ __global__ void __launch_bounds__(kElocWarps * 32) eloc_sliced_kernel(int B, int
                                                                      const int32_t* __restrict__ field,
                                                                      const int32_t* __restrict__ slice,
                                                                      int32_t* __restrict__ part, int ldp) {
-  extern __shared__ uint32_t bits[];  // [n]
+  // STAGE: the word's n spin words in shared memory; otherwise read through
+  // L1 (no shared memory, so that the CTAs fit beside a GEMM's)
+  extern __shared__ uint32_t staged[];  // [n] if STAGE
   __shared__ uint32_t planes[kElocWarps][32];
   __shared__ int32_t fpart[kElocWarps][32];
   __shared__ int32_t wpart[kElocWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wd = blockIdx.x, q = blockIdx.y;
   const uint32_t* src = Sbits + (size_t)wd * n;
-  for (int i = threadIdx.x; i < n; i += kElocWarps * 32) bits[i] = __ldg(src + i);
-  __syncthreads();
+  if constexpr (STAGE) {
+    for (int i = threadIdx.x; i < n; i += kElocWarps * 32) staged[i] = __ldg(src + i);
+    __syncthreads();
+  }
+  auto bit_word = [&](int i) -> uint32_t {
+    if constexpr (STAGE) return staged[i];
+    else return __ldg(src + i);
+  };
   const int r0 = __ldg(slice + q), r1 = __ldg(slice + q + 1);
   // the field: lane = sample, as in the plain kernel
   int32_t fe = 0;
   if (field)
     for (int i = r0 + warp; i < r1; i += kElocWarps) {
       const int32_t f = __ldg(field + i);
-      fe += ((bits[i] >> lane) & 1u) ? -f : f;
+      fe += ((bit_word(i) >> lane) & 1u) ? -f : f;
     }
   const int pa = __ldg(row_ptr + r0), pb = __ldg(row_ptr + r1);
   uint32_t C[32];
@@ -163,7 +171,7 @@ __global__ void __launch_bounds__(kElocWarps * 32) eloc_sliced_kernel(int B, int
     for (int t = 0; t < PL; ++t) L[t] = 0u;
     for (int k = 0; k < 15 && p < pb; ++k, p += kElocWarps * 32) {
       const int32_t wt = __ldg(w + p);
-      const uint32_t x = bits[__ldg(erow + p)] ^ bits[__ldg(col + p)];
+      const uint32_t x = bit_word(__ldg(erow + p)) ^ bit_word(__ldg(col + p));
       ws += wt;
       uint32_t c = 0;
 #pragma unroll
@@ -263,16 +271,50 @@ struct StatAcc<float> {
   static __device__ __forceinline__ M hi() { return -1.0 / 0.0; }
 };
 
+template <typename V>
+__device__ __forceinline__ V shfl_down_v(V v, int d) {
+  return __shfl_down_sync(0xffffffffu, v, d);
+}
+
+// Sum, min and max over the CTA (warp shuffles, then one warp over the 32
+// warps' values): the result in every thread.  Fixed order.
+template <typename S, typename M>
+__device__ __forceinline__ void cta_reduce(S& sum, M& mn, M& mx, S* ws, M* wmn, M* wmx) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    sum += shfl_down_v(sum, d);
+    const M a = shfl_down_v(mn, d), b = shfl_down_v(mx, d);
+    mn = a < mn ? a : mn;
+    mx = b > mx ? b : mx;
+  }
+  if (lane == 0) ws[warp] = sum, wmn[warp] = mn, wmx[warp] = mx;
+  __syncthreads();
+  if (warp == 0) {
+    sum = ws[lane], mn = wmn[lane], mx = wmx[lane];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      sum += shfl_down_v(sum, d);
+      const M a = shfl_down_v(mn, d), b = shfl_down_v(mx, d);
+      mn = a < mn ? a : mn;
+      mx = b > mx ? b : mx;
+    }
+    if (lane == 0) ws[0] = sum, wmn[0] = mn, wmx[0] = mx;
+  }
+  __syncthreads();
+  sum = ws[0], mn = wmn[0], mx = wmx[0];
+}
+
 template <typename A>
 __global__ void __launch_bounds__(1024) stats_kernel(int B, const A* __restrict__ E, double* __restrict__ out,
                                                      float* __restrict__ coef, uint32_t* __restrict__ err,
                                                      DevState* ds, float beta1, float beta2) {
   using S = typename StatAcc<A>::S;
   using M = typename StatAcc<A>::M;
-  __shared__ S s_sum[1024];
-  __shared__ M s_min[1024], s_max[1024];
-  __shared__ double s_var[1024];
-  __shared__ double s_mean;
+  __shared__ S ws[32];
+  __shared__ M wmn[32], wmx[32];
+  __shared__ double wv[32];
+  __shared__ M dummy_mn[32], dummy_mx[32];
   const int t = threadIdx.x;
   if (ds && t == 0) {
     ds->adam_t += 1;
@@ -280,49 +322,32 @@ __global__ void __launch_bounds__(1024) stats_kernel(int B, const A* __restrict_
   }
   S sum = 0;
   M mn = StatAcc<A>::lo(), mx = StatAcc<A>::hi();
-  for (int b = t; b < B; b += 1024) {
+  for (int b = t; b < B; b += blockDim.x) {
     const A x = E[b];
     sum += (S)x;
     mn = (M)x < mn ? (M)x : mn;
     mx = (M)x > mx ? (M)x : mx;
   }
-  s_sum[t] = sum;
-  s_min[t] = mn;
-  s_max[t] = mx;
-  __syncthreads();
-  for (int o = 512; o > 0; o >>= 1) {
-    if (t < o) {
-      s_sum[t] += s_sum[t + o];
-      s_min[t] = s_min[t + o] < s_min[t] ? s_min[t + o] : s_min[t];
-      s_max[t] = s_max[t + o] > s_max[t] ? s_max[t + o] : s_max[t];
-    }
-    __syncthreads();
-  }
-  if (t == 0) s_mean = (double)s_sum[0] / (double)B;
-  __syncthreads();
-  const double mean = s_mean;
+  cta_reduce(sum, mn, mx, ws, wmn, wmx);
+  const double mean = (double)sum / (double)B;
   double ss = 0.0;
-  for (int b = t; b < B; b += 1024) {
+  for (int b = t; b < B; b += blockDim.x) {
     const double d = (double)E[b] - mean;
     ss += d * d;
   }
-  s_var[t] = ss;
-  __syncthreads();
-  for (int o = 512; o > 0; o >>= 1) {
-    if (t < o) s_var[t] += s_var[t + o];
-    __syncthreads();
-  }
+  M u0 = 0, u1 = 0;
+  cta_reduce(ss, u0, u1, wv, dummy_mn, dummy_mx);
   if (t == 0) {
-    const double var = s_var[0] / (double)B;
+    const double var = ss / (double)B;
     out[0] = mean;
     out[1] = var;
-    out[2] = (double)s_min[0];
-    out[3] = (double)s_max[0];
+    out[2] = (double)mn;
+    out[3] = (double)mx;
     if (!isfinite(mean) || !isfinite(var)) atomicOr(err, kErrNonfinite);
   }
   if (coef) {
     const double inv = 1.0 / (double)B;
-    for (int b = t; b < B; b += 1024) coef[b] = (float)(((double)E[b] - mean) * inv);
+    for (int b = t; b < B; b += blockDim.x) coef[b] = (float)(((double)E[b] - mean) * inv);
   }
 }
 
@@ -368,9 +393,9 @@ __global__ void tile_sum_kernel(int cnt, int ntiles, const float* __restrict__ p
 }  // namespace
 
 template <int PL>
-cudaError_t eloc_sliced(const vqmc_ctx* c, int B, void* d_e, cudaStream_t st) {
-  const size_t smem = (size_t)c->n * sizeof(uint32_t);
-  auto k = eloc_sliced_kernel<PL>;
+cudaError_t eloc_sliced(const vqmc_ctx* c, int B, void* d_e, cudaStream_t st, bool stage) {
+  const size_t smem = stage ? (size_t)c->n * sizeof(uint32_t) : 0;
+  auto k = stage ? eloc_sliced_kernel<PL, true> : eloc_sliced_kernel<PL, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int ns = c->eloc_slices;
@@ -398,14 +423,16 @@ cudaError_t eloc_sparse(const vqmc_ctx* c, int B, void* d_e, cudaStream_t st) {
 }
 
 cudaError_t launch_eloc_sparse(const vqmc_ctx* c, int B, const int8_t* d_s, void* d_e, cudaStream_t st,
-                               bool packed) {
+                               bool packed, bool beside) {
   if (B <= 0) return cudaSuccess;
   if (!packed) pack_bits_kernel<<<dim3((c->n + 255) / 256, (B + 31) / 32), 256, 0, st>>>(B, c->n, d_s, c->Sbits);
   if (c->ham == VQMC_HAM_SPARSE_I32) {
     // weights of at most 8 bits (magnitude): the bit-sliced kernel
-    if (c->eloc_wbits <= 1) return eloc_sliced<6>(c, B, d_e, st);
-    if (c->eloc_wbits <= 4) return eloc_sliced<9>(c, B, d_e, st);
-    if (c->eloc_wbits <= 8) return eloc_sliced<13>(c, B, d_e, st);
+    // beside: the launch shares the GPU with a GEMM, so the spin words are
+    // read through L1 instead of taking shared memory
+    if (c->eloc_wbits <= 1) return eloc_sliced<6>(c, B, d_e, st, !beside);
+    if (c->eloc_wbits <= 4) return eloc_sliced<9>(c, B, d_e, st, !beside);
+    if (c->eloc_wbits <= 8) return eloc_sliced<13>(c, B, d_e, st, !beside);
     return eloc_sparse<int32_t, int32_t>(c, B, d_e, st);
   }
   return eloc_sparse<float, float>(c, B, d_e, st);

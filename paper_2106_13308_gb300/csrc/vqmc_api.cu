@@ -604,7 +604,7 @@ vqmc_status vqmc_step(vqmc_ctx* c, int32_t B, vqmc_stream stream, vqmc_step_stat
   if (overlap) {
     VQ_CUDA(cudaEventRecord(c->ev_fork, st));
     VQ_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    VQ_CUDA(launch_eloc_sparse(c, B, c->S, c->E, c->side, /*packed=*/tc));
+    VQ_CUDA(launch_eloc_sparse(c, B, c->S, c->E, c->side, /*packed=*/tc, /*beside=*/true));
     VQ_CUDA(launch_stats(c, B, c->E, c->stats, c->coef, c->side, /*advance=*/true));
     VQ_CUDA(cudaEventRecord(c->ev_join, c->side));
     VQ_CUDA(launch_gemm(c, kOpHidden, B, c->S, nullptr, nullptr, st));
