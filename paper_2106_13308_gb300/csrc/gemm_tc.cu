@@ -250,13 +250,14 @@ __global__ void __launch_bounds__(kThreads, Stages<KC>::kMinBlocks)
   constexpr bool kWgrad = op == kOpDV || op == kOpDW;
   const bool fused = kWgrad && g.theta != nullptr;
   // Tiles in launch order, heaviest K range first where the masks make the
-  // ranges uneven (the hidden GEMM: K grows with the N-tile; the hidden
-  // adjoint: K shrinks with it), so that the last wave holds the light tiles.
+  // ranges uneven (the hidden GEMM and the output GEMM: K grows with the
+  // N-tile; the hidden adjoint: K shrinks with it), so that the last wave
+  // holds the light tiles.
   int tm = blockIdx.y, tn = blockIdx.x;
-  if constexpr (OP == kOpHidden || OP == kOpGA) {
+  if constexpr (OP == kOpHidden || OP == kOpGA || OP == kOpOut) {
     const int L = blockIdx.y * gridDim.x + blockIdx.x;  // launch order
     tm = L % gridDim.y;
-    tn = OP == kOpHidden ? (int)gridDim.x - 1 - L / (int)gridDim.y : L / (int)gridDim.y;
+    tn = OP == kOpGA ? L / (int)gridDim.y : (int)gridDim.x - 1 - L / (int)gridDim.y;
   }
   const int m0 = tm * BM, n0 = tn * BN;
   const int m1 = min(m0 + BM, g.M), n1 = min(n0 + BN, g.N);
