@@ -248,21 +248,12 @@ __global__ void eloc_dense_finish_kernel(int B, int n, int ntiles, const float* 
 
 // FP64 statistics of B energies in one CTA with a fixed reduction order.
 // With ds set, thread 0 also starts the next Adam step (t += 1 and its bias
-// corrections), which the gradient kernels after it read.  FP64 arithmetic
-// is slow on this part, so integer energies are summed in int64 and their
-// extremes taken in int32 (exact: the same mean as an FP64 sum, whose
-// partial sums are exact integers), and the coefficients (E_b - mean) / B
-// multiply by 1 / B (exact for B a power of two; otherwise within one
-// rounding of the quotient before the conversion to FP32).
+// corrections), which the gradient kernels after it read.  Float energies
+// (this kernel); the coefficients (E_b - mean) / B multiply by 1 / B (exact
+// for B a power of two; otherwise within one rounding of the quotient before
+// the conversion to FP32).  Integer energies: stats_int_kernel below.
 template <typename A>
 struct StatAcc;
-template <>
-struct StatAcc<int32_t> {
-  using S = long long;
-  using M = int32_t;
-  static __device__ __forceinline__ M lo() { return 0x7fffffff; }
-  static __device__ __forceinline__ M hi() { return -0x7fffffff - 1; }
-};
 template <>
 struct StatAcc<float> {
   using S = double;
@@ -348,6 +339,77 @@ __global__ void __launch_bounds__(1024) stats_kernel(int B, const A* __restrict_
   if (coef) {
     const double inv = 1.0 / (double)B;
     for (int b = t; b < B; b += blockDim.x) coef[b] = (float)(((double)E[b] - mean) * inv);
+  }
+}
+
+// Integer energies: the same statistics with integer arithmetic only
+// (FP64 is slow on this part).  mean = S / B from S = sum E (int64); the
+// variance (B Q - S^2) / B^2 from Q = sum E^2 (128-bit integers: exact before
+// its one rounding); the coefficients (B E_b - S) / B^2 as an FP32 product,
+// equal to the FP64 path's (E_b - mean) / B rounded to FP32 when B is a power
+// of two (otherwise within about one rounding of it).
+__global__ void __launch_bounds__(1024) stats_int_kernel(int B, const int32_t* __restrict__ E, double* __restrict__ out,
+                                                         float* __restrict__ coef, uint32_t* __restrict__ err,
+                                                         DevState* ds, float beta1, float beta2) {
+  __shared__ long long ws[32];
+  __shared__ unsigned long long wql[32];
+  __shared__ long long wqh[32];
+  __shared__ int32_t wmn[32], wmx[32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = (int)(blockDim.x >> 5);
+  if (ds && t == 0) {
+    ds->adam_t += 1;
+    adam_factors(ds, beta1, beta2);
+  }
+  long long sum = 0;
+  __int128 sq = 0;
+  int32_t mn = 0x7fffffff, mx = -0x7fffffff - 1;
+  for (int b = t; b < B; b += blockDim.x) {
+    const long long x = E[b];
+    sum += x;
+    sq += (__int128)(x * x);
+    mn = (int32_t)x < mn ? (int32_t)x : mn;
+    mx = (int32_t)x > mx ? (int32_t)x : mx;
+  }
+  auto reduce_warp = [&]() {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      sum += __shfl_down_sync(0xffffffffu, sum, d);
+      const unsigned long long lo = (unsigned long long)sq, olo = __shfl_down_sync(0xffffffffu, lo, d);
+      const long long hi = (long long)(sq >> 64), ohi = __shfl_down_sync(0xffffffffu, hi, d);
+      sq += (__int128)(((unsigned __int128)(unsigned long long)ohi << 64) | olo);
+      const int32_t a = __shfl_down_sync(0xffffffffu, mn, d), c = __shfl_down_sync(0xffffffffu, mx, d);
+      mn = a < mn ? a : mn;
+      mx = c > mx ? c : mx;
+    }
+  };
+  reduce_warp();
+  if (lane == 0) ws[warp] = sum, wql[warp] = (unsigned long long)sq, wqh[warp] = (long long)(sq >> 64),
+                 wmn[warp] = mn, wmx[warp] = mx;
+  __syncthreads();
+  if (warp == 0) {
+    sum = lane < nw ? ws[lane] : 0;
+    sq = lane < nw ? (__int128)(((unsigned __int128)(unsigned long long)wqh[lane] << 64) | wql[lane]) : 0;
+    mn = lane < nw ? wmn[lane] : 0x7fffffff;
+    mx = lane < nw ? wmx[lane] : -0x7fffffff - 1;
+    reduce_warp();
+    if (lane == 0) ws[0] = sum, wql[0] = (unsigned long long)sq, wqh[0] = (long long)(sq >> 64), wmn[0] = mn, wmx[0] = mx;
+  }
+  __syncthreads();
+  const long long S = ws[0];
+  const double mean = (double)S / (double)B;
+  if (t == 0) {
+    const __int128 Q = (__int128)(((unsigned __int128)(unsigned long long)wqh[0] << 64) | wql[0]);
+    const __int128 num = (__int128)B * Q - (__int128)S * (__int128)S;  // B^2 var >= 0
+    const double var = (double)num / ((double)B * (double)B);
+    out[0] = mean;
+    out[1] = var;
+    out[2] = (double)wmn[0];
+    out[3] = (double)wmx[0];
+    if (!isfinite(mean) || !isfinite(var)) atomicOr(err, kErrNonfinite);
+  }
+  if (coef) {
+    const float inv2 = (float)(1.0 / ((double)B * (double)B));
+    for (int b = t; b < B; b += blockDim.x) coef[b] = (float)((long long)B * E[b] - S) * inv2;
   }
 }
 
@@ -452,7 +514,7 @@ cudaError_t launch_stats(const vqmc_ctx* c, int B, const void* d_e, double* d_st
   DevState* ds = advance ? c->dstate : nullptr;
   const float b1 = c->cfg.beta1, b2 = c->cfg.beta2;
   if (c->ham == VQMC_HAM_SPARSE_I32)
-    stats_kernel<int32_t><<<1, 1024, 0, st>>>(B, (const int32_t*)d_e, d_stats, d_coef, c->err, ds, b1, b2);
+    stats_int_kernel<<<1, 1024, 0, st>>>(B, (const int32_t*)d_e, d_stats, d_coef, c->err, ds, b1, b2);
   else
     stats_kernel<float><<<1, 1024, 0, st>>>(B, (const float*)d_e, d_stats, d_coef, c->err, ds, b1, b2);
   return cudaGetLastError();
