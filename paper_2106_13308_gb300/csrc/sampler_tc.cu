@@ -31,8 +31,8 @@
 // the update GEMM's operand; while they solve, warps 2-3 merge the previous
 // block's recent g1 into the Z operand, prepare the next block's logits and
 // recent-unit weights and write out the previous block's spins; warp 4 lane 0
-// streams 128 x 64 BF16 weight tiles with TMA into a 6-stage ring; warp 5
-// lane 0 issues the MMAs.  Every wait is bounded; after a failed wait the CTA
+// streams 128 x 64 BF16 weight tiles with TMA into a ring of six tiles,
+// consumed in two slots of three; warp 5 lane 0 issues the MMAs.  Every wait is bounded; after a failed wait the CTA
 // raises the timeout bit and runs on without waiting, so it still finishes.
 #include <algorithm>
 #include <type_traits>
@@ -176,8 +176,9 @@ __device__ __forceinline__ float g1f(float a) {
   else return 1.0f / (1.0f + expf(-a));
 }
 
-// The sequential part of a block: the draws of its D steps, carried by
-// lanes 4s..4s+3 of warps 2-3 for sample s.  With sorted degrees at most
+// The sequential part of a block: the draws of its D steps, carried for
+// sample s by solver threads 8s .. 8s+7 (kLanes lanes of one warp of the
+// solver warps 0, 1, 6 and 7).  With sorted degrees at most
 // one hidden unit completes per step (h < n), and the logit of step e
 // depends on the earlier spins only through the units completed before e:
 //     z_e = (Z_e + b2) + sum_{recent r: t_r < e} W2_{e,r} g1_r,
