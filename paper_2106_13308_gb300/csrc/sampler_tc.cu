@@ -147,7 +147,9 @@ __device__ __forceinline__ uint64_t bf2(uint32_t w) { return pk2(bf_lo(w), bf_hi
 // slots from a busy warp on the same sub-partition
 // The same wait polling with mbarrier.test_wait, which returns at once: for
 // the MMA issuer's waits on landed tiles, which are usually already complete
-// (a try_wait there costs the issuing thread about 190 cycles even then).
+// (a try_wait there costs the issuing thread about 190 cycles even then),
+// and for the single threads of the producer and the MMA issuer on the
+// block hand-offs, where a try_wait's suspension delays the reaction.
 __device__ __forceinline__ bool test_or_abort(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t* err) {
   for (long long it = 0; it < kSpinLimit; ++it) {
     if (mbar_test_wait(bar, parity)) return true;
@@ -503,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int cnt = min(kSlotTiles, i1 - i);
           const int s = it % kNSlot;
           if (it >= kNSlot &&
-              !wait_or_abort(smem_u32(&empty[s]), (uint32_t)((it / kNSlot - 1) & 1), abort, g.err))
+              !test_or_abort(smem_u32(&empty[s]), (uint32_t)((it / kNSlot - 1) & 1), abort, g.err))
             return false;
           const uint32_t bar = smem_u32(&full[s]);
           mbar_expect_tx(bar, (uint32_t)(cnt * kTileBytes));
@@ -584,7 +586,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const Blk B = blk_of(b, n, h, D, ntiles, nblk);
         const uint32_t s_prev = base + kOffS + ((b - 1) & 1) * (kDmax / 64) * 2048;
         if (b > 0 && ok) {
-          ok = wait_or_abort(smem_u32(ready), (uint32_t)((b - 1) & 1), abort, g.err, true);
+          ok = test_or_abort(smem_u32(ready), (uint32_t)((b - 1) & 1), abort, g.err);
           fence_after();
         }
         // update tiles: index q -> accumulator of unit tile q / nkd, K-chunk q % nkd of block b-1's spins
@@ -601,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         else mbar_arrive(smem_u32(zfull));
         if (ok) ok = mma_phase(B.bulk0 * nkd, ntiles * nkd, upd);
         if (B.np > 0 && ok) {
-          ok = wait_or_abort(smem_u32(merged), (uint32_t)(b & 1), abort, g.err, true);
+          ok = test_or_abort(smem_u32(merged), (uint32_t)(b & 1), abort, g.err);
           fence_after();
           const uint32_t zn = kZCol + 16 * ((b + 1) & 1);
           if (ok)
