@@ -230,7 +230,11 @@ vqmc_status vqmc_logprob_backward(vqmc_ctx* ctx, int32_t B, const int8_t* d_s, c
 /* FP64 batch statistics of energies d_e (int32 or float32 per instance kind):
  * d_stats double [4] = {mean, var, min, max} (var with 1/B), and, if d_coef
  * is not NULL, the score-function coefficients c_b = (E_b - mean)/B as
- * float32 [B].  A non-finite value sets VQMC_DEVERR_NONFINITE. */
+ * float32 [B].  For int32 energies the sums of E and E^2 are exact integers
+ * (64 and 128 bits) and mean and var are each rounded once to FP64; c_b is
+ * (B E_b - sum E) / B^2 rounded to float32 (exactly so when B is a power of
+ * two).  Float energies accumulate in FP64 in a fixed order.  A non-finite
+ * value sets VQMC_DEVERR_NONFINITE. */
 vqmc_status vqmc_energy_stats(vqmc_ctx* ctx, int32_t B, const void* d_e, double* d_stats, float* d_coef,
                               vqmc_stream stream);
 
