@@ -691,12 +691,23 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      // the 16 samples of each step (stt, sbits): a warp transposes a word of
+      // 32 steps with ballots (lane s < 16 holds sample s's word; ballot j
+      // collects step j's spins) and lane j keeps step j's column
+      const uint32_t valid = b0 + kS <= g.B ? 0xFFFFu : (1u << (g.B - b0)) - 1u;  // samples inside B
       if (g.stt || g.sbits)
-        for (int e = t0; e < steps; e += nt) {
-          uint32_t dn = 0;  // bit s: sample b0 + s has spin -1 at step e
+        for (int w = t0 >> 5; w < (steps + 31) / 32; w += nt >> 5) {
+          const int ln = t0 & 31;
+          const uint32_t word = ln < kS ? sb[ln * (kDmax / 32) + w] : 0u;
+          uint32_t up = 0;
 #pragma unroll
-          for (int s = 0; s < kS; ++s)
-            if (b0 + s < g.B && !((sb[s * (kDmax / 32) + (e >> 5)] >> (e & 31)) & 1u)) dn |= 1u << s;
+          for (int j = 0; j < 32; ++j) {
+            const uint32_t col = __ballot_sync(0xffffffffu, (word >> j) & 1u);
+            up = ln == j ? col : up;
+          }
+          const int e = 32 * w + ln;
+          if (e >= steps) continue;
+          const uint32_t dn = ~up & valid;  // bit s: sample b0 + s has spin -1 at step e
           if (g.stt) {
             bf16* dt = g.stt + (size_t)(b * D + e) * g.ldst + b0;
             if (b0 + kS <= g.B && (reinterpret_cast<uintptr_t>(dt) & 15) == 0) {
