@@ -216,7 +216,8 @@ __device__ __forceinline__ void solve(const float* Pr, const bf16* Vr, const bf1
   // helpers below): in segment r only units 0 .. r-1 are complete (g1 != 0
   // in hh) and only units r .. 31 still need partial sums, so the logit's dot
   // product reads the 8-unit chunks 0 .. PH, the weight-row update writes the
-  // chunks PH .. 3 and the completing unit's partial sum is one of 16.  The
+  // chunks PH .. 3 and the completing unit's partial sum is one of 16 (8 in
+  // the last phase).  The
   // skipped terms are zeros (g1 of incomplete units) or sums never read
   // again, so the draws are those of the full loops.
   // Z_e + b2 + the terms of the recent units completed so far (hh, chunks 0 .. PH)
